@@ -1,0 +1,360 @@
+// Fused red + black Gauss-Seidel sweep for sm_103a (one launch = one full sweep of a level).
+//
+// Equivalent, bit for bit, to: fill ghosts, red half-sweep, fill ghosts, black half-sweep.
+// The source phi has 2 ghost layers and rhs 1, both filled beforehand.  A CTA owns one
+// (box, y-tile) and streams its z-planes through shared memory:
+//   * TMA bulk copies (cp.async.bulk, one per plane) bring phi rows [y0-2, y0+TY+2) and rhs
+//     rows [y0-1, y0+TY+1) of each plane into a ring of shared-memory buffers, completing on
+//     mbarriers; loads run D planes ahead of the compute;
+//   * stage s red-updates plane s over the tile plus a one-cell ring (the ring cells belong
+//     to neighbouring tiles / boxes / periodic images and are recomputed redundantly from the
+//     second ghost layer -- exactly the values their owners compute), then black-updates
+//     plane s-1 using those red values;
+//   * the finished plane s-1 goes back to global memory by one bulk store of whole rows into
+//     the destination buffer (a second phi allocation: tiles read each other's rows as
+//     halos, so the sweep cannot be done in place).
+// Ghost cells outside the domain (Dirichlet faces) are never updated: a boundary cell's
+// ghost equals -(its own value before this half-sweep), which the fill already holds for
+// every cell that the half-sweep updates.
+//
+// Every mbarrier wait is bounded; on expiry the CTA records an error code, drains its own
+// outstanding copies (again bounded) and returns.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mg_kernels.hpp"
+
+namespace gbmg {
+
+namespace {
+
+template <class T>
+struct Ar;
+template <>
+struct Ar<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+};
+template <>
+struct Ar<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+constexpr long long kSpinLimit = 1ll << 26;  // polls before a wait is declared stuck
+
+// Bounded wait on one phase of an mbarrier.  Returns false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <class T>
+struct Sweep {
+  // per-CTA constants
+  const DRow* R;
+  int y0, ty;            // tile rows [y0, y0+ty)
+  int nx, ny, nz;
+  int pitch, pr;         // phi / rhs pitches (elements)
+  int g, gr;             // ghost widths
+  long long plane, planer;
+  int flags;             // bit d: low face of dim d is a Dirichlet domain face; bit 3+d: high
+  uint32_t pbytes, rbytes;
+  T h2;
+  int lox, loy, loz;
+};
+
+}  // namespace
+
+// Shared memory: NP phi buffers, NR rhs buffers, then NP + NR mbarriers.
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_rbgs_fused(const DRow* __restrict__ rows,
+                                                    const int2* __restrict__ units, int ty_max,
+                                                    unsigned phi_buf_elems, unsigned rhs_buf_elems,
+                                                    int* __restrict__ err) {
+  constexpr int NP = 4 + D;  // live phi planes s-2..s+1 plus D in flight
+  constexpr int NR = 2 + D;  // live rhs planes s-1, s plus D in flight
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* pbuf = (T*)smem;
+  T* rbuf = pbuf + (size_t)NP * phi_buf_elems;
+  uint64_t* bars = (uint64_t*)(rbuf + (size_t)NR * rhs_buf_elems);
+  uint64_t* pbar = bars;
+  uint64_t* rbar = bars + NP;
+
+  const int2 u = units[blockIdx.x];
+  const DRow& R = rows[u.x];
+  Sweep<T> S;
+  S.nx = R.n[0];
+  S.ny = R.n[1];
+  S.nz = R.n[2];
+  S.y0 = u.y;
+  S.ty = min(ty_max, S.ny - S.y0);
+  S.pitch = R.v[0].pitch;
+  S.plane = R.v[0].plane;
+  S.g = R.v[0].g;
+  S.pr = R.v[1].pitch;
+  S.planer = R.v[1].plane;
+  S.gr = R.v[1].g;
+  S.flags = R.pad_;
+  S.h2 = (T)R.h2;
+  S.lox = R.lo[0];
+  S.loy = R.lo[1];
+  S.loz = R.lo[2];
+  S.pbytes = (uint32_t)((S.ty + 4) * S.pitch * sizeof(T));
+  S.rbytes = (uint32_t)((S.ty + 2) * S.pr * sizeof(T));
+
+  const T* src = (const T*)R.v[0].p;  // valid cell (0,0,0) of the source phi
+  const T* rhs = (const T*)R.v[1].p;
+  T* dst = (T*)R.v[2].p;              // valid cell (0,0,0) of the destination phi
+  const int tid = threadIdx.x;
+  const int nzl = S.nz;
+
+  if (tid == 0) {
+    for (int i = 0; i < NP + NR; ++i) mbar_init(&bars[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // global row starts (x = -g) of the first loaded row of plane p
+  auto phi_src = [&](int p) {
+    return src + (long long)p * S.plane + (long long)(S.y0 - 2) * S.pitch - S.g;
+  };
+  auto rhs_src = [&](int p) {
+    return rhs + (long long)p * S.planer + (long long)(S.y0 - 1) * S.pr - S.gr;
+  };
+  auto pslot = [&](int p) { return (p + 2 * NP) % NP; };  // p >= -2
+  auto rslot = [&](int p) { return (p + 2 * NR) % NR; };
+  // number of times a slot has been loaded before plane p (for the mbarrier parity)
+  auto pphase = [&](int p) { return (uint32_t)(((p + 2) / NP) & 1); };
+  auto rphase = [&](int p) { return (uint32_t)(((p + 1) / NR) & 1); };
+
+  const int pmax = nzl + 1;  // last phi plane loaded
+  const int rmax = nzl;      // last rhs plane loaded
+  int p_issued = -3, r_issued = -2;  // last issued plane
+  auto issue_phi = [&](int p) {
+    if (p > pmax) return;
+    uint64_t* b = &pbar[pslot(p)];
+    mbar_expect_tx(b, S.pbytes);
+    bulk_load(pbuf + (size_t)pslot(p) * phi_buf_elems, phi_src(p), S.pbytes, b);
+    p_issued = p;
+  };
+  auto issue_rhs = [&](int p) {
+    if (p > rmax) return;
+    uint64_t* b = &rbar[rslot(p)];
+    mbar_expect_tx(b, S.rbytes);
+    bulk_load(rbuf + (size_t)rslot(p) * rhs_buf_elems, rhs_src(p), S.rbytes, b);
+    r_issued = p;
+  };
+
+  // Prologue: before stage s, phi planes up to s+D and rhs planes up to s+D-1 are queued.
+  if (tid == 0) {
+    for (int p = -2; p <= -1 + D; ++p) issue_phi(p);
+    for (int p = -1; p <= -2 + D; ++p) issue_rhs(p);
+  }
+
+  bool ok = true;
+  int p_done = -3, r_done = -2;  // planes every thread has seen land
+  for (int s = -1; s <= nzl; ++s) {
+    // Inputs of stage s: phi planes s-1..s+1 and rhs plane s (earlier planes landed in
+    // earlier stages).  Every thread waits on the barriers of the planes it reads.
+    for (int p = (s == -1 ? -2 : s + 1); p <= s + 1; ++p)
+      if (!mbar_wait_bounded(&pbar[pslot(p)], pphase(p))) ok = false;
+    if (!mbar_wait_bounded(&rbar[rslot(s)], rphase(s))) ok = false;
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      break;
+    }
+    p_done = s + 1;
+    r_done = s;
+
+    T* P0 = pbuf + (size_t)pslot(s - 1) * phi_buf_elems;
+    T* P1 = pbuf + (size_t)pslot(s) * phi_buf_elems;
+    T* P2 = pbuf + (size_t)pslot(s + 1) * phi_buf_elems;
+    const T* Q = rbuf + (size_t)rslot(s) * rhs_buf_elems;
+    // element (x, y) of a phi buffer: [(y - y0 + 2) * pitch + x + g]; rhs: [(y - y0 + 1) * pr + x + gr]
+    const int gz = S.loz + s;
+    // ---- red half of plane s
+    {
+      bool ghost_plane = (s < 0 || s >= nzl);
+      bool skip = (s < 0 && (S.flags & 4)) || (s >= nzl && (S.flags & 32));
+      if (!skip) {
+        // rows / columns of the red region
+        int ya = ghost_plane ? S.y0 : S.y0 - 1;
+        int yb = ghost_plane ? S.y0 + S.ty - 1 : S.y0 + S.ty;
+        if (!ghost_plane) {
+          if (ya < 0 && (S.flags & 2)) ya = 0;
+          if (yb >= S.ny && (S.flags & 16)) yb = S.ny - 1;
+        }
+        int xa = ghost_plane ? 0 : -1, xb = ghost_plane ? S.nx - 1 : S.nx;
+        if (!ghost_plane) {
+          if (S.flags & 1) xa = 0;
+          if (S.flags & 8) xb = S.nx - 1;
+        }
+        const int nrow = yb - ya + 1;
+        const int npair = (xb - xa + 2) / 2;
+        for (int idx = tid; idx < nrow * npair; idx += blockDim.x) {
+          int y = ya + idx / npair;
+          int pr = idx % npair;
+          int gy = S.loy + y;
+          // first x >= xa with (lo + x + gy + gz) even
+          int x = xa + ((S.lox + xa + gy + gz) & 1) + 2 * pr;
+          if (x > xb) continue;
+          bool yin = y >= 0 && y < S.ny, xin = x >= 0 && x < S.nx;
+          if (!yin && !xin) continue;  // ring corner: not a neighbour of a tile cell
+          int o = (y - S.y0 + 2) * S.pitch + x + S.g;
+          T a = P1[o - 1];
+          a = Ar<T>::add(a, P1[o + 1]);
+          a = Ar<T>::add(a, P1[o - S.pitch]);
+          a = Ar<T>::add(a, P1[o + S.pitch]);
+          a = Ar<T>::add(a, P0[o]);
+          a = Ar<T>::add(a, P2[o]);
+          T q = Q[(y - S.y0 + 1) * S.pr + x + S.gr];
+          P1[o] = Ar<T>::div(Ar<T>::sub(a, Ar<T>::mul(S.h2, q)), (T)6);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- black half of plane s-1 (tile cells only)
+    const int pb = s - 1;
+    if (pb >= 0 && pb < nzl) {
+      T* B0 = pbuf + (size_t)pslot(pb - 1) * phi_buf_elems;
+      T* B1 = P0;
+      T* B2 = P1;
+      const T* QB = rbuf + (size_t)rslot(pb) * rhs_buf_elems;
+      const int gzb = S.loz + pb;
+      const int npair = (S.nx + 1) / 2;
+      for (int idx = tid; idx < S.ty * npair; idx += blockDim.x) {
+        int y = S.y0 + idx / npair;
+        int pr = idx % npair;
+        int gy = S.loy + y;
+        int x = ((S.lox + gy + gzb + 1) & 1) + 2 * pr;
+        if (x >= S.nx) continue;
+        int o = (y - S.y0 + 2) * S.pitch + x + S.g;
+        T a = B1[o - 1];
+        a = Ar<T>::add(a, B1[o + 1]);
+        a = Ar<T>::add(a, B1[o - S.pitch]);
+        a = Ar<T>::add(a, B1[o + S.pitch]);
+        a = Ar<T>::add(a, B0[o]);
+        a = Ar<T>::add(a, B2[o]);
+        T q = QB[(y - S.y0 + 1) * S.pr + x + S.gr];
+        B1[o] = Ar<T>::div(Ar<T>::sub(a, Ar<T>::mul(S.h2, q)), (T)6);
+      }
+      fence_async_smem();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      if (pb >= 0 && pb < nzl) {
+        // whole rows y0..y0+ty-1 of plane pb (x ghosts of the destination get overwritten;
+        // they are refilled before they are read)
+        T* gdst = dst + (long long)pb * S.plane + (long long)S.y0 * S.pitch - S.g;
+        bulk_store(gdst, P0 + 2 * S.pitch, (uint32_t)(S.ty * S.pitch * sizeof(T)));
+      }
+      bulk_commit();
+      bulk_wait_read1();  // the buffer reused below was stored two stages ago
+      issue_phi(s + 1 + D);
+      issue_rhs(s + D);
+    }
+  }
+  // Drain: wait (bounded) for every load this CTA issued but did not consume -- at most
+  // D + 2 per ring, so each slot holds one outstanding phase -- and for the stores, so no
+  // copy touches shared memory after the CTA exits.
+  if (tid == 0) {
+    for (int p = p_done + 1; p <= p_issued; ++p) mbar_wait_bounded(&pbar[pslot(p)], pphase(p));
+    for (int p = r_done + 1; p <= r_issued; ++p) mbar_wait_bounded(&rbar[rslot(p)], rphase(p));
+    bulk_wait_all();
+  }
+  __syncthreads();
+}
+
+template <class T, int D>
+static cudaError_t launch_fused_t(const DRow* rows, const int2* units, int nunits, int ty,
+                                  int max_pitch, int max_pitch_r, int* err, cudaStream_t s) {
+  constexpr int NP = 4 + D, NR = 2 + D;
+  unsigned pe = (unsigned)((ty + 4) * max_pitch);
+  unsigned re = (unsigned)((ty + 2) * max_pitch_r);
+  const unsigned align = 128 / sizeof(T);
+  pe = (pe + align - 1) / align * align;
+  re = (re + align - 1) / align * align;
+  size_t smem = ((size_t)NP * pe + (size_t)NR * re) * sizeof(T) + (NP + NR) * 8;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_rbgs_fused<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_rbgs_fused<T, D><<<nunits, 256, smem, s>>>(rows, units, ty, pe, re, err);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+size_t fused_smem_bytes(int dt, int ty, int max_pitch, int max_pitch_r, int depth) {
+  size_t es = dt == DT_F64 ? 8 : 4;
+  int NP = 4 + depth, NR = 2 + depth;
+  size_t align = 128 / es;
+  size_t pe = ((size_t)(ty + 4) * max_pitch + align - 1) / align * align;
+  size_t re = ((size_t)(ty + 2) * max_pitch_r + align - 1) / align * align;
+  return (NP * pe + NR * re) * es + (NP + NR) * 8;
+}
+
+cudaError_t launch_rbgs_fused(int dt, const DRow* rows, const int2* units, int nunits, int ty,
+                              int depth, int max_pitch, int max_pitch_r, int* err,
+                              cudaStream_t s) {
+  if (nunits <= 0) return cudaSuccess;
+  if (dt == DT_F64) {
+    if (depth <= 1) return launch_fused_t<double, 1>(rows, units, nunits, ty, max_pitch, max_pitch_r, err, s);
+    return launch_fused_t<double, 2>(rows, units, nunits, ty, max_pitch, max_pitch_r, err, s);
+  }
+  if (depth <= 1) return launch_fused_t<float, 1>(rows, units, nunits, ty, max_pitch, max_pitch_r, err, s);
+  return launch_fused_t<float, 2>(rows, units, nunits, ty, max_pitch, max_pitch_r, err, s);
+}
+
+}  // namespace gbmg

@@ -1,0 +1,581 @@
+// Kernels of the multigrid path on sm_103a: ghost fill over copy tags, red-black
+// Gauss-Seidel half-sweeps, residual with fused max-norm, fused residual + restriction,
+// restriction, prolongation, bottom solve and the mixed-precision scale / correction.
+//
+// All stencil kernels are bounded by HBM bandwidth (about 1 flop per byte), so none of them
+// uses the tensor cores.  Each launch covers every box of its table (Sec. 3.2 kernel fusing).
+// Arithmetic goes through __{d,f}{add,sub,mul,div}_rn so that no multiply is contracted into
+// an FMA: every operation is one IEEE round-to-nearest step in the documented order.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+
+#include "mg_kernels.hpp"
+
+namespace gbmg {
+
+namespace {
+
+template <class T>
+struct Ar;
+template <>
+struct Ar<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+};
+template <>
+struct Ar<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+};
+
+constexpr int kWarps = 8;  // warps per block in the row kernels
+constexpr int kThreads = kWarps * 32;
+
+__device__ __forceinline__ int find_box(const DRow* __restrict__ rows, int nbox, long long r) {
+  int lo = 0, hi = nbox - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (rows[mid].row0 <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Block k owns rows [k*per, (k+1)*per); warp w of the block takes rows begin+w, +kWarps, ...
+// f(box, row-within-box) is called once per row with all 32 lanes active.
+template <class F>
+__device__ __forceinline__ void for_rows(const DRow* __restrict__ rows, int nbox, long long nrows,
+                                         long long per, F&& f) {
+  long long begin = (long long)blockIdx.x * per;
+  long long end = begin + per < nrows ? begin + per : nrows;
+  long long r = begin + (threadIdx.x >> 5);
+  if (r >= end) return;
+  int b = find_box(rows, nbox, r);
+  for (; r < end; r += kWarps) {
+    while (b + 1 < nbox && rows[b + 1].row0 <= r) ++b;
+    f(b, r - rows[b].row0);
+  }
+}
+
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Sum of the six neighbours of p[0] in the order x-, x+, y-, y+, z-, z+.
+template <class T>
+__device__ __forceinline__ T nbr_sum(const T* p, int pitch, long long plane) {
+  T s = p[-1];
+  s = Ar<T>::add(s, p[1]);
+  s = Ar<T>::add(s, p[-pitch]);
+  s = Ar<T>::add(s, p[pitch]);
+  s = Ar<T>::add(s, p[-plane]);
+  s = Ar<T>::add(s, p[plane]);
+  return s;
+}
+
+template <class T>
+__device__ __forceinline__ T* line(const DView& v, int y, int z) {
+  return (T*)v.p + (long long)z * v.plane + (long long)y * v.pitch;
+}
+
+// ---------------------------------------------------------------------------------------
+// Copy tags (ghost fill, dense scatter / gather).  One warp per chunk of kTagChunk
+// destination cells of one tag; lanes walk the tag region x fastest.
+template <class T>
+__global__ void __launch_bounds__(256) k_copy_tags(const DTag* __restrict__ tags,
+                                                   const int2* __restrict__ chunks, int nchunks,
+                                                   void* const* __restrict__ bases, int ncomp) {
+  int w = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (w >= nchunks) return;
+  const int lane = threadIdx.x & 31;
+  const int2 ch = chunks[w];
+  const DTag t = tags[ch.x];
+  const int ncell = t.ex * t.ey * t.ez;
+  const int end = min(ch.y + kTagChunk, ncell);
+  const T* __restrict__ src = (const T*)bases[t.base_src];
+  T* __restrict__ dst = (T*)bases[t.base_dst];
+  for (int l = ch.y + lane; l < end; l += 32) {
+    int x = l % t.ex;
+    int q = l / t.ex;
+    int y = q % t.ey;
+    int z = q / t.ey;
+    long long so = t.src + (long long)x * t.ssx + (long long)y * t.ssy + (long long)z * t.ssz;
+    long long d = t.dst + x + (long long)y * t.dsy + (long long)z * t.dsz;
+    for (int c = 0; c < ncomp; ++c) {
+      T v;
+      if (t.sign == 0) v = T(0);
+      else if (t.sign > 0) v = src[so + c * t.scs];
+      else v = -src[so + c * t.scs];
+      dst[d + c * t.dcs] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Red-black Gauss-Seidel half-sweep: cells with (i+j+k) mod 2 == color (global indices)
+// take phi = (s - h^2 rhs) / 6.  Lane l of a warp updates cells par + 2l (+64 k) of a line.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_rbgs_half(const DRow* __restrict__ rows, int nbox,
+                                                        long long nrows, long long per, int color) {
+  const int lane = threadIdx.x & 31;
+  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
+    const DRow& R = rows[b];
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const DView vp = R.v[0];
+    T* phi = line<T>(vp, y, z);
+    const T* rhs = line<T>(R.v[1], y, z);
+    const T h2 = (T)R.h2;
+    const int par = (color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1;
+    for (int x = par + 2 * lane; x < n0; x += 64) {
+      T s = nbr_sum(phi + x, vp.pitch, vp.plane);
+      phi[x] = Ar<T>::div(Ar<T>::sub(s, Ar<T>::mul(h2, rhs[x])), (T)6);
+    }
+  });
+}
+
+// Flush per-warp maxima: each warp stores (solve, max); thread 0 merges equal solves.
+__device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
+                                                unsigned long long* norms) {
+  __shared__ unsigned long long s_max[kWarps];
+  __shared__ int s_sol[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  mx = warp_max(mx);
+  if (lane == 0) { s_max[warp] = mx; s_sol[warp] = cur; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int sol = -1;
+    unsigned long long acc = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      if (s_sol[w] < 0) continue;
+      if (s_sol[w] != sol) {
+        if (sol >= 0 && acc) atomicMax(&norms[sol], acc);
+        sol = s_sol[w];
+        acc = 0;
+      }
+      acc = s_max[w] > acc ? s_max[w] : acc;
+    }
+    if (sol >= 0 && acc) atomicMax(&norms[sol], acc);
+  }
+}
+
+// Residual r = rhs - (s - 6 phi) * (1/h^2), optionally stored, with a fused max-norm.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_residual(const DRow* __restrict__ rows, int nbox,
+                                                       long long nrows, long long per,
+                                                       unsigned long long* norms) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long mx = 0;
+  int cur = -1;
+  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
+    const DRow& R = rows[b];
+    if (R.solve != cur) {
+      if (cur >= 0 && norms) {
+        unsigned long long m = warp_max(mx);
+        if (lane == 0 && m) atomicMax(&norms[cur], m);
+      }
+      cur = R.solve;
+      mx = 0;
+    }
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const DView vp = R.v[0];
+    const T* phi = line<T>(vp, y, z);
+    const T* rhs = line<T>(R.v[1], y, z);
+    T* r = R.v[2].p ? line<T>(R.v[2], y, z) : nullptr;
+    const T ih2 = (T)R.ih2;
+    for (int x = lane; x < n0; x += 32) {
+      T s = nbr_sum(phi + x, vp.pitch, vp.plane);
+      T v = Ar<T>::sub(rhs[x], Ar<T>::mul(Ar<T>::sub(s, Ar<T>::mul((T)6, phi[x])), ih2));
+      if (r) r[x] = v;
+      unsigned long long bits = (unsigned long long)__double_as_longlong(fabs((double)v));
+      mx = bits > mx ? bits : mx;
+    }
+  });
+  if (norms) flush_block_max(mx, cur, norms);
+}
+
+// Fused residual + restriction.  Lane l of a warp produces coarse cells X = l, l+32, ... of
+// one coarse x-line: the 8 child residuals summed x fastest, times 1/8.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_residual_restrict(const DRow* __restrict__ rows,
+                                                                int nbox, long long nrows,
+                                                                long long per) {
+  const int lane = threadIdx.x & 31;
+  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
+    const DRow& R = rows[b];
+    const int nc0 = R.n[0] >> 1, nc1 = R.n[1] >> 1;
+    const int Y = (int)(lr % nc1), Z = (int)(lr / nc1);
+    const DView vp = R.v[0], vr = R.v[1];
+    const T ih2 = (T)R.ih2;
+    T* crhs = line<T>(R.c[0], Y, Z);
+    T* cphi = R.c[1].p ? line<T>(R.c[1], Y, Z) : nullptr;
+    for (int X = lane; X < nc0; X += 32) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const T* p = line<T>(vp, 2 * Y + j, 2 * Z + k) + 2 * X + i;
+            const T* q = line<T>(vr, 2 * Y + j, 2 * Z + k) + 2 * X + i;
+            T s = nbr_sum(p, vp.pitch, vp.plane);
+            T v = Ar<T>::sub(q[0], Ar<T>::mul(Ar<T>::sub(s, Ar<T>::mul((T)6, p[0])), ih2));
+            acc = (i | j | k) ? Ar<T>::add(acc, v) : v;
+          }
+      crhs[X] = Ar<T>::mul(acc, (T)0.125);
+      if (cphi) cphi[X] = T(0);
+    }
+  });
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_restrict(const DRow* __restrict__ rows, int nbox,
+                                                       long long nrows, long long per) {
+  const int lane = threadIdx.x & 31;
+  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
+    const DRow& R = rows[b];
+    const int nc0 = R.n[0] >> 1, nc1 = R.n[1] >> 1;
+    const int Y = (int)(lr % nc1), Z = (int)(lr / nc1);
+    T* c = line<T>(R.c[0], Y, Z);
+    for (int X = lane; X < nc0; X += 32) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            T v = line<T>(R.v[0], 2 * Y + j, 2 * Z + k)[2 * X + i];
+            acc = (i | j | k) ? Ar<T>::add(acc, v) : v;
+          }
+      c[X] = Ar<T>::mul(acc, (T)0.125);
+    }
+  });
+}
+
+// fine(c) += coarse(floor(c / 2)); c[0] addresses coarse cell floor(lo / 2).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_prolong_add(const DRow* __restrict__ rows, int nbox,
+                                                          long long nrows, long long per) {
+  const int lane = threadIdx.x & 31;
+  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
+    const DRow& R = rows[b];
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const int ox = R.lo[0] & 1, oy = R.lo[1] & 1, oz = R.lo[2] & 1;
+    T* f = line<T>(R.v[0], y, z);
+    const T* c = line<T>(R.c[0], (y + oy) >> 1, (z + oz) >> 1);
+    for (int x = lane; x < n0; x += 32) f[x] = Ar<T>::add(f[x], c[(x + ox) >> 1]);
+  });
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_set_valid(const DRow* __restrict__ rows, int nbox,
+                                                        long long nrows, long long per, T value) {
+  const int lane = threadIdx.x & 31;
+  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
+    const DRow& R = rows[b];
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    T* f = line<T>(R.v[0], y, z);
+    for (int x = lane; x < n0; x += 32) f[x] = value;
+  });
+}
+
+template <class T>
+__global__ void k_set_flat(T* p, long long n, T value) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = value;
+}
+
+// Exact bottom solve: one block per job, rhs gathered to shared memory in FP64.
+template <class T>
+__global__ void k_bottom(const BottomJob* __restrict__ jobs) {
+  extern __shared__ double sb[];
+  const BottomJob J = jobs[blockIdx.x];
+  const T* rhs = (const T*)J.rhs;
+  T* phi = (T*)J.phi;
+  for (int j = threadIdx.x; j < J.N; j += blockDim.x) sb[j] = (double)rhs[J.off_rhs[j]];
+  __syncthreads();
+  for (int i = threadIdx.x; i < J.N; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < J.N; ++j) s = __dadd_rn(s, __dmul_rn(J.Mt[(long long)j * J.N + i], sb[j]));
+    phi[J.off_phi[i]] = (T)s;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_dense_copy(const DRow* __restrict__ rows, int nbox,
+                                                         long long nrows, long long per, T* dense,
+                                                         int3 dlo, int3 dn, int ncomp,
+                                                         int to_dense) {
+  const int lane = threadIdx.x & 31;
+  const long long dplane = (long long)dn.x * dn.y, dcomp = dplane * dn.z;
+  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
+    const DRow& R = rows[b];
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    T* f = line<T>(R.v[0], y, z);
+    T* d = dense + (long long)(R.lo[2] + z - dlo.z) * dplane +
+           (long long)(R.lo[1] + y - dlo.y) * dn.x + (R.lo[0] - dlo.x);
+    for (int c = 0; c < ncomp; ++c) {
+      T* fc = f + c * R.v[0].cstride;
+      T* dc = d + c * dcomp;
+      if (to_dense) {
+        for (int x = lane; x < n0; x += 32) dc[x] = fc[x];
+      } else {
+        for (int x = lane; x < n0; x += 32) fc[x] = dc[x];
+      }
+    }
+  });
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_maxabs(const DRow* __restrict__ rows, int nbox,
+                                                     long long nrows, long long per,
+                                                     unsigned long long* norms) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long mx = 0;
+  int cur = -1;
+  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
+    const DRow& R = rows[b];
+    if (R.solve != cur) {
+      if (cur >= 0) {
+        unsigned long long m = warp_max(mx);
+        if (lane == 0 && m) atomicMax(&norms[cur], m);
+      }
+      cur = R.solve;
+      mx = 0;
+    }
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const T* f = line<T>(R.v[0], y, z);
+    for (int x = lane; x < n0; x += 32) {
+      unsigned long long bits = (unsigned long long)__double_as_longlong(fabs((double)f[x]));
+      mx = bits > mx ? bits : mx;
+    }
+  });
+  flush_block_max(mx, cur, norms);
+}
+
+__device__ __forceinline__ double norm_of(const unsigned long long* norms, int solve) {
+  return __longlong_as_double((long long)norms[solve]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_residual_scale_f32(const DRow* __restrict__ rows,
+                                                                 int nbox, long long nrows,
+                                                                 long long per,
+                                                                 const unsigned long long* norms) {
+  const int lane = threadIdx.x & 31;
+  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
+    const DRow& R = rows[b];
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const DView vp = R.v[0];
+    const double* phi = line<double>(vp, y, z);
+    const double* rhs = line<double>(R.v[1], y, z);
+    float* r32 = line<float>(R.c[0], y, z);
+    const double ih2 = R.ih2;
+    const double sc = norm_of(norms, R.solve);
+    for (int x = lane; x < n0; x += 32) {
+      double s = nbr_sum(phi + x, vp.pitch, vp.plane);
+      double v = __dsub_rn(rhs[x], __dmul_rn(__dsub_rn(s, __dmul_rn(6.0, phi[x])), ih2));
+      r32[x] = __double2float_rn(__ddiv_rn(v, sc));
+    }
+  });
+}
+
+__global__ void __launch_bounds__(kThreads) k_correct_add(const DRow* __restrict__ rows, int nbox,
+                                                          long long nrows, long long per,
+                                                          const unsigned long long* norms) {
+  const int lane = threadIdx.x & 31;
+  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
+    const DRow& R = rows[b];
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    double* phi = line<double>(R.v[0], y, z);
+    const float* e = line<float>(R.c[0], y, z);
+    const double sc = norm_of(norms, R.solve);
+    for (int x = lane; x < n0; x += 32) phi[x] = __dadd_rn(phi[x], __dmul_rn(sc, (double)e[x]));
+  });
+}
+
+struct Grid {
+  long long per;
+  unsigned blocks;
+};
+
+Grid row_grid(long long nrows, int blocks_per_sm) {
+  long long target = (long long)num_sms() * blocks_per_sm;
+  long long per = (nrows + target - 1) / target;
+  if (per < kWarps) per = kWarps;
+  Grid g;
+  g.per = per;
+  g.blocks = (unsigned)((nrows + per - 1) / per);
+  return g;
+}
+
+}  // namespace
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches += n; }
+long long launches_so_far() { return g_launches.load(); }
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 1;
+  }
+  return n;
+}
+
+cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int nchunks,
+                             void* const* bases, int ncomp, cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  unsigned blocks = (unsigned)((nchunks + 7) / 8);
+  if (dt == DT_F64) k_copy_tags<double><<<blocks, 256, 0, s>>>(tags, chunks, nchunks, bases, ncomp);
+  else k_copy_tags<float><<<blocks, 256, 0, s>>>(tags, chunks, nchunks, bases, ncomp);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
+                             cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  if (dt == DT_F64) k_rbgs_half<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, color);
+  else k_rbgs_half<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, color);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
+                            unsigned long long* norms, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 4);
+  if (dt == DT_F64) k_residual<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
+  else k_residual<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_restrict(int dt, const DRow* rows, int nbox, long long nrows,
+                                     cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  if (dt == DT_F64) k_residual_restrict<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
+  else k_residual_restrict<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  if (dt == DT_F64) k_restrict<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
+  else k_restrict<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(int dt, const DRow* rows, int nbox, long long nrows,
+                               cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  if (dt == DT_F64) k_prolong_add<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
+  else k_prolong_add<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bottom(int dt, const BottomJob* jobs, int njobs, int maxN, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  int threads = maxN < 32 ? 32 : (maxN > 1024 ? 1024 : (maxN + 31) / 32 * 32);
+  size_t smem = (size_t)maxN * sizeof(double);
+  if (dt == DT_F64) k_bottom<double><<<njobs, threads, smem, s>>>(jobs);
+  else k_bottom<float><<<njobs, threads, smem, s>>>(jobs);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_valid(int dt, const DRow* rows, int nbox, long long nrows, double value,
+                             cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  if (dt == DT_F64) k_set_valid<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, value);
+  else k_set_valid<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, (float)value);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_flat(int dt, void* p, long long n, double value, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  long long cap = (long long)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  if (dt == DT_F64) k_set_flat<double><<<(unsigned)blocks, 256, 0, s>>>((double*)p, n, value);
+  else k_set_flat<float><<<(unsigned)blocks, 256, 0, s>>>((float*)p, n, (float)value);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_copy(int dt, const DRow* rows, int nbox, long long nrows, void* dense,
+                              const int dom_lo[3], const int dom_n[3], int ncomp, int to_dense,
+                              cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  int3 lo = make_int3(dom_lo[0], dom_lo[1], dom_lo[2]);
+  int3 n = make_int3(dom_n[0], dom_n[1], dom_n[2]);
+  if (dt == DT_F64)
+    k_dense_copy<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, (double*)dense, lo, n, ncomp, to_dense);
+  else
+    k_dense_copy<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, (float*)dense, lo, n, ncomp, to_dense);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxabs(int dt, const DRow* rows, int nbox, long long nrows,
+                          unsigned long long* norms, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 4);
+  if (dt == DT_F64) k_maxabs<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
+  else k_maxabs<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_scale_f32(const DRow* rows, int nbox, long long nrows,
+                                      const unsigned long long* norms, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  k_residual_scale_f32<<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_correct_add(const DRow* rows, int nbox, long long nrows,
+                               const unsigned long long* norms, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  k_correct_add<<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace gbmg

@@ -1,0 +1,135 @@
+// Device-side tables and kernel launchers of the multigrid path (sm_103a).
+//
+// Every stencil operation is one launch over all boxes of a level (or of several levels of
+// several solves): the launch walks a device "box table" of DRow entries, the analogue of
+// the array of Array4 views behind the fused ParallelFor of Sec. 3.2 of the AMReX/pyAMReX
+// review.  The ghost fill walks a device copy-tag table (Sec. 2 cached communication
+// patterns, Sec. 3.5 fused pack/unpack).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbmg {
+
+enum { DT_F64 = 0, DT_F32 = 1 };
+
+// View of one box of a fab: p addresses the first valid cell (local (0,0,0), component 0);
+// cell (x,y,z) is p[z*plane + y*pitch + x], ghosts at negative / >= n local indices.
+struct DView {
+  void* p;
+  long long plane;
+  long long cstride;  // elements per component
+  int pitch;
+  int g;
+};
+
+// One box of a level in a stencil launch.  row0 is the first "row" (an x-line, or a coarse
+// x-line for restriction) of this box in the launch's row space; rows of a box are ordered
+// y fastest, then z.
+struct DRow {
+  int lo[3];
+  int n[3];
+  int solve;     // slot in per-solve arrays (norms, scales)
+  int pad_;
+  long long row0;
+  double h2;     // h*h of this level
+  double ih2;    // 1/(h*h)
+  DView v[3];    // op-specific fine views (see each launcher)
+  DView c[2];    // op-specific coarse views, addressing coarse cell floor(lo/2)
+};
+
+// Ghost-fill / dense-copy tag: destination cells dst + x + y*dsy + z*dsz (0 <= x < ex ...)
+// take sign * src[src + x*ssx + y*ssy + z*ssz]; components at +c*dcs / +c*scs.  Offsets are
+// in elements from bases[base_dst] / bases[base_src].  sign 0 writes 0.
+struct DTag {
+  long long src, dst;
+  long long scs, dcs;
+  int ssx, ssy, ssz;
+  int dsy, dsz;
+  int ex, ey, ez;
+  int sign;
+  int base_src, base_dst;
+  int pad_;
+};
+
+// Exact bottom solve of one level: phi[off_phi[i]] = sum_j Mt[j*N + i] * rhs[off_rhs[j]].
+struct BottomJob {
+  const double* Mt;        // transposed (pseudo-)inverse, N x N
+  const long long* off_rhs;
+  const long long* off_phi;
+  const void* rhs;
+  void* phi;
+  int N;
+  int pad_;
+};
+
+constexpr int kTagChunk = 128;  // destination cells per warp in the copy-tag kernel
+
+int num_sms();
+
+// Process-wide count of kernels enqueued by the launchers below (plus graph kernel nodes
+// per replay, added by the graph owner).
+void count_launches(long long n);
+long long launches_so_far();
+
+cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int nchunks,
+                             void* const* bases, int ncomp, cudaStream_t s);
+
+// v[0] = phi (ghosts filled), v[1] = rhs.
+cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
+                             cudaStream_t s);
+
+// v[0] = phi, v[1] = rhs, v[2] = r (p == null: not stored).  norms[solve] receives
+// atomicMax of the bit pattern of |r| (NaN propagates as the largest pattern).
+cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
+                            unsigned long long* norms, cudaStream_t s);
+
+// Rows are coarse x-lines.  v[0] = phi, v[1] = rhs (fine); c[0] = coarse rhs,
+// c[1] = coarse phi (p == null: not zeroed).
+cudaError_t launch_residual_restrict(int dt, const DRow* rows, int nbox, long long nrows,
+                                     cudaStream_t s);
+
+// Rows are coarse x-lines.  v[0] = fine field; c[0] = coarse field.
+cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows, cudaStream_t s);
+
+// Rows are fine x-lines.  v[0] = fine field (+=); c[0] = coarse field.
+cudaError_t launch_prolong_add(int dt, const DRow* rows, int nbox, long long nrows,
+                               cudaStream_t s);
+
+// Fused red + black sweep (see mg_fused.cu).  Rows: v[0] = source phi (2 ghost layers,
+// filled), v[1] = rhs (1 ghost layer, filled), v[2] = destination phi with the source's
+// layout; pad_ = Dirichlet-face flags (bit d: low face of dim d, bit 3+d: high face).
+// units[i] = {box, y0} tiles of height ty; depth = planes loaded ahead (1 or 2).
+size_t fused_smem_bytes(int dt, int ty, int max_pitch, int max_pitch_r, int depth);
+cudaError_t launch_rbgs_fused(int dt, const DRow* rows, const int2* units, int nunits, int ty,
+                              int depth, int max_pitch, int max_pitch_r, int* err,
+                              cudaStream_t s);
+
+cudaError_t launch_bottom(int dt, const BottomJob* jobs, int njobs, int maxN, cudaStream_t s);
+
+// v[0] = field: valid cells = value.
+cudaError_t launch_set_valid(int dt, const DRow* rows, int nbox, long long nrows, double value,
+                             cudaStream_t s);
+// Whole allocation (ghosts and padding included) = value.
+cudaError_t launch_set_flat(int dt, void* p, long long n, double value, cudaStream_t s);
+
+// Dense domain array (ncomp, nz, ny, nx) <-> valid cells of a fab; v[0] = fab view (with
+// cstride).  to_dense: 1 copies fab -> dense, 0 dense -> fab.
+cudaError_t launch_dense_copy(int dt, const DRow* rows, int nbox, long long nrows, void* dense,
+                              const int dom_lo[3], const int dom_n[3], int ncomp, int to_dense,
+                              cudaStream_t s);
+
+// max |value| over valid cells, atomicMax of bit patterns into norms[solve]; v[0] = field.
+cudaError_t launch_maxabs(int dt, const DRow* rows, int nbox, long long nrows,
+                          unsigned long long* norms, cudaStream_t s);
+
+// Mixed precision.  v[0] = phi (FP64, ghosts filled), v[1] = rhs (FP64), c[0].p = r32 out
+// (FP32, a view with the same box geometry): r32 = float(r / s), s = norms[solve].
+cudaError_t launch_residual_scale_f32(const DRow* rows, int nbox, long long nrows,
+                                      const unsigned long long* norms, cudaStream_t s);
+// v[0] = phi (FP64), c[0] = e (FP32 view, same geometry): phi = phi + s * double(e).
+cudaError_t launch_correct_add(const DRow* rows, int nbox, long long nrows,
+                               const unsigned long long* norms, cudaStream_t s);
+
+}  // namespace gbmg

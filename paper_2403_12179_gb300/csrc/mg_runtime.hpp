@@ -1,0 +1,260 @@
+// Runtime objects behind the C ABI: context, stream-ordered memory pool, box arrays, fabs,
+// cached ghost-fill plans and stencil tables, multigrid hierarchies.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/gbmg.h"
+#include "mg_host.hpp"
+#include "mg_kernels.hpp"
+
+namespace gbmg {
+
+struct MgError {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+void set_last_error(const std::string& msg);
+
+// Runs f() and converts exceptions into MG_E* codes plus the thread's last-error message.
+template <class F>
+int guard(F&& f) {
+  try {
+    set_last_error("");
+    return f();
+  } catch (const MgError& e) {
+    set_last_error(e.msg);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host out of memory");
+    return MG_ENOMEM;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return MG_EINVAL;
+  }
+}
+#define MG_CK(call) ::gbmg::check_cuda((call), #call)
+
+struct Ctx;
+
+// Device memory from the context pool, released in stream order.
+struct DevBuf {
+  Ctx* ctx = nullptr;
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf();
+  void reset(cudaStream_t s);
+};
+using DevBufP = std::unique_ptr<DevBuf>;
+
+struct BoxArrayObj {
+  BoxArray ba;
+  bool levels_built = false;
+  bool levels_ok = false;
+  std::string levels_err;
+  std::vector<BoxArray> levels;
+  const std::vector<BoxArray>& hierarchy();  // throws MG_EINVAL if no valid hierarchy
+};
+
+// A ghost-fill plan: device copy tags + chunk list for one fab and one set of BCs.
+struct FillPlan {
+  std::vector<DTag> host_tags;  // offsets relative to the fab base (base index 0)
+  DevBufP tags, chunks, bases;
+  int nchunks = 0;
+};
+
+struct FabObj {
+  int64_t id = 0;
+  int64_t ba_id = 0;
+  std::shared_ptr<BoxArrayObj> ba;
+  FabLayout lay;
+  int dtype = DT_F64;
+  void* base = nullptr;
+  size_t bytes = 0;
+  DevBufP own;  // null for wrapped memory
+  std::map<int, std::unique_ptr<FillPlan>> fills;  // key: bc code
+  DevBufP valid_rows;  // DRow table, v[0] = this fab (fine x-lines)
+  long long nrows = 0;
+  std::shared_ptr<FabObj> partner;  // same-layout scratch for out-of-place sweeps
+  DView view(int b) const;
+  int esize() const { return dtype == DT_F64 ? 8 : 4; }
+};
+
+struct OpTable {
+  DevBufP d;
+  int nbox = 0;
+  long long nrows = 0;
+  const DRow* rows() const { return d ? (const DRow*)d->p : nullptr; }
+};
+
+struct Hierarchy;
+
+struct Ctx {
+  int device = -1;
+  cudaStream_t stream = nullptr;   // context stream (solves)
+  cudaStream_t own_stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  size_t pool_cap = 0;
+  std::atomic<size_t> in_use{0};
+  std::mutex mu;  // guards the handle maps and the pool accounting
+  std::map<int64_t, std::shared_ptr<BoxArrayObj>> bas;
+  std::map<int64_t, std::shared_ptr<FabObj>> fabs;
+  int64_t next_id = 1;
+  std::chrono::steady_clock::time_point t0;
+  std::vector<std::shared_ptr<Hierarchy>> hier;   // cached solver hierarchies
+  std::map<std::string, std::vector<double>> bottom_cache;  // key -> transposed M
+  // device error word written by kernels whose bounded waits expire (0 = fine)
+  DevBufP d_err;
+  // scratch for norms (device) and its pinned host mirror
+  DevBufP d_norms;
+  unsigned long long* h_norms = nullptr;
+  int norm_slots = 0;
+  // cached stencil tables of the level-operation entry points, keyed by op, fabs and h
+  struct CachedOp {
+    std::vector<int64_t> fabs;
+    OpTable t;
+  };
+  std::map<std::string, CachedOp> op_cache;
+  std::map<std::string, std::shared_ptr<struct FusedTable>> fused_cache;
+  // serving
+  struct Server;
+  std::shared_ptr<Server> server;
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  void require_device() const {
+    if (device < 0) fail(MG_EINVAL, "host-only context: no device memory or kernels");
+  }
+  DevBufP alloc(size_t bytes, cudaStream_t s);
+  DevBufP upload(const void* host, size_t bytes, cudaStream_t s);
+  std::shared_ptr<BoxArrayObj> get_ba(int64_t id);
+  std::shared_ptr<FabObj> get_fab(int64_t id);
+  int64_t add_ba(std::shared_ptr<BoxArrayObj> b);
+  void ensure_norm_slots(int n);
+};
+
+int bc_code(const mg_bc* bc, int periodic[3]);  // validates; returns a small cache key
+
+// Plans and tables ----------------------------------------------------------------------
+FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc);
+void launch_fill(Ctx& c, FabObj& f, const mg_bc* bc, cudaStream_t s);
+void ensure_valid_rows(Ctx& c, FabObj& f);
+
+// Appends one row per box of `ba` to a host table; views(b, row) fills the views of box b.
+// kind 0: rows are fine x-lines; kind 1: rows are coarse x-lines (n/2 of each dimension).
+template <class F>
+void append_rows(std::vector<DRow>* rows, long long* nrows, const BoxArray& ba, int kind,
+                 double h, int solve, F&& views) {
+  for (size_t b = 0; b < ba.boxes.size(); ++b) {
+    DRow R{};
+    const Box& B = ba.boxes[b];
+    for (int d = 0; d < 3; ++d) { R.lo[d] = B.lo[d]; R.n[d] = B.len(d); }
+    R.solve = solve;
+    R.row0 = *nrows;
+    R.h2 = h * h;
+    R.ih2 = 1.0 / (h * h);
+    views((int)b, R);
+    *nrows += kind == 0 ? (long long)R.n[1] * R.n[2] : (long long)(R.n[1] / 2) * (R.n[2] / 2);
+    rows->push_back(R);
+  }
+}
+OpTable upload_table(Ctx& c, const std::vector<DRow>& rows, long long nrows, cudaStream_t s);
+
+template <class F>
+OpTable make_table(Ctx& c, const BoxArray& ba, int kind, double h, int solve, F&& views,
+                   cudaStream_t s) {
+  std::vector<DRow> rows;
+  long long n = 0;
+  append_rows(&rows, &n, ba, kind, h, solve, views);
+  return upload_table(c, rows, n, s);
+}
+
+// Cached table for a level operation on the given fabs (built on the context stream).
+template <class B>
+const OpTable& op_table(Ctx& c, const char* op, std::vector<int64_t> ids, double h, B&& build) {
+  std::string key = op;
+  for (int64_t id : ids) key += ":" + std::to_string(id);
+  unsigned long long hb;
+  static_assert(sizeof hb == sizeof h, "");
+  std::memcpy(&hb, &h, sizeof h);
+  key += ":" + std::to_string(hb);
+  auto it = c.op_cache.find(key);
+  if (it != c.op_cache.end()) return it->second.t;
+  OpTable t = build();
+  check_cuda(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+  auto& e = c.op_cache[key];
+  e.fabs = std::move(ids);
+  e.t = std::move(t);
+  return e.t;
+}
+void drop_cached_ops_of(Ctx& c, int64_t fab_id);
+
+// Fused red + black sweep table: rows (src, rhs, dst views + Dirichlet-face flags) and
+// (box, y0) tiles.  ok == false when the layout cannot use the fused kernel.
+struct FusedTable {
+  bool ok = false;
+  OpTable rows;
+  DevBufP units;
+  int nunits = 0, ty = 16, depth = 2, max_pitch = 0, max_pitch_r = 0;
+  std::vector<int64_t> owner_fabs;  // for cache invalidation
+};
+bool fused_eligible(const FabObj& phi, const FabObj& rhs);
+FusedTable make_fused(Ctx& c, const BoxArray& ba, double h, const FabObj& src, const FabObj& rhs,
+                      const FabObj& dst, const int periodic[3], int ty, cudaStream_t s);
+void launch_fused(Ctx& c, const FusedTable& t, int dt, cudaStream_t s);
+// Cached fused table for (src, rhs, dst, bc, h); src/rhs/dst ids are the fab handles (0 for
+// internal fabs, which must then be cached by their owner instead).
+const FusedTable& fused_table(Ctx& c, int64_t src_id, FabObj& src, int64_t rhs_id, FabObj& rhs,
+                              int64_t dst_id, FabObj& dst, const mg_bc* bc, double h);
+std::shared_ptr<FabObj> partner_of(Ctx& c, FabObj& f);
+void check_device_error(Ctx& c);
+
+// Copy-tag conversion to device layout (offsets relative to the fab base).
+std::vector<DTag> device_tags(const BoxArray& ba, const FabLayout& lay,
+                              const std::vector<CopyTag>& tags, int base_index);
+
+// Hierarchy / solve -----------------------------------------------------------------------
+struct SolveParams {
+  int nu1 = 2, nu2 = 2, max_iter = 50, precision = MG_PREC_F64, smoother = MG_SMOOTH_AUTO;
+  int use_graph = 1, fixed_vcycles = -1;
+  double h = 0.0;
+};
+SolveParams params_from(const mg_options* o, const BoxArray& ba);
+
+int solve(Ctx& c, int64_t rhs, int64_t phi, const mg_bc* bc, double tol, const SolveParams& p,
+          mg_result* res);
+int solve_batch(Ctx& c, int n, const int64_t* rhs, const int64_t* phi, const mg_bc* bcs,
+                double tol, const SolveParams& p, mg_result* res);
+void drop_hierarchies_of(Ctx& c, int64_t fab_id);
+void destroy_hierarchies(Ctx& c);
+
+// Serving
+int server_submit(Ctx& c, int64_t rhs, int64_t phi, const mg_bc* bc, double tol,
+                  const SolveParams& p, int64_t* ticket);
+int server_poll(Ctx& c, int64_t ticket, int timeout_ms, mg_result* res);
+void server_stop(Ctx& c);
+
+// Bottom matrix (transposed), cached per (n, periodic, h).
+const std::vector<double>& bottom_matrix_t(Ctx& c, const int n[3], const int periodic[3],
+                                           double h);
+
+}  // namespace gbmg

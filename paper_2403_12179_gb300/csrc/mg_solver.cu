@@ -1,0 +1,478 @@
+// Multigrid hierarchy and V-cycle driver.
+//
+// The paper (Sec. 2) only names a cell-centered linear solver; the cycle here is the one
+// this library documents in gbmg.h: V(nu1, nu2) with red-black Gauss-Seidel, fused
+// residual + restriction, piecewise-constant prolongation and an exact bottom solve, the
+// stop test ||rhs - A phi||_inf <= tol ||rhs||_inf before each cycle.  Each stage is one
+// launch over all boxes of a level; a whole cycle plus the next norm check is replayed as
+// one CUDA graph.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "mg_runtime.hpp"
+
+namespace gbmg {
+
+namespace {
+
+std::shared_ptr<FabObj> internal_fab(Ctx& c, std::shared_ptr<BoxArrayObj> ba, int g, int dt) {
+  auto f = std::make_shared<FabObj>();
+  f->ba = std::move(ba);
+  f->dtype = dt;
+  f->lay = make_layout(f->ba->ba, 1, g, f->esize());
+  f->bytes = (size_t)f->lay.total * f->esize();
+  f->own = c.alloc(f->bytes, c.stream);
+  f->base = f->own->p;
+  MG_CK(cudaMemsetAsync(f->base, 0, f->bytes, c.stream));
+  return f;
+}
+
+bool same_boxes(const BoxArray& a, const BoxArray& b) {
+  return a.boxes.size() == b.boxes.size() &&
+         std::memcmp(a.boxes.data(), b.boxes.data(), a.boxes.size() * sizeof(Box)) == 0 &&
+         std::memcmp(&a.dom, &b.dom, sizeof(Box)) == 0;
+}
+
+DView coarse_view_of(const FabObj& coarse, const Box& fine_box) {
+  const BoxArray& C = coarse.ba->ba;
+  Box p;
+  for (int d = 0; d < 3; ++d) { p.lo[d] = fdiv2(fine_box.lo[d]); p.hi[d] = fdiv2(fine_box.hi[d]); }
+  for (size_t cb = 0; cb < C.boxes.size(); ++cb) {
+    if (intersect(p, C.boxes[cb]).npts() != p.npts()) continue;
+    DView v = coarse.view((int)cb);
+    const Box& B = C.boxes[cb];
+    long long o = (long long)(p.lo[2] - B.lo[2]) * v.plane + (long long)(p.lo[1] - B.lo[1]) * v.pitch +
+                  (p.lo[0] - B.lo[0]);
+    v.p = (char*)v.p + o * coarse.esize();
+    return v;
+  }
+  fail(MG_EINVAL, "internal: parent cells span several coarse boxes");
+}
+
+}  // namespace
+
+struct LevelData {
+  std::shared_ptr<BoxArrayObj> bao;
+  double h = 1.0;
+  std::shared_ptr<FabObj> phi, rhs;
+  OpTable smooth, rr, prolong, zero;
+  // fused sweeps ping-pong between phi and phi2 (same layout)
+  bool fused = false;
+  std::shared_ptr<FabObj> phi2;
+  FusedTable f_ab, f_ba;
+};
+
+struct Hierarchy {
+  // cache key
+  int64_t rhs_id = 0, phi_id = 0;
+  int bc_key = 0;
+  SolveParams p;
+  mg_bc bc{};
+  int dt = DT_F64;  // inner precision
+  bool mixed = false;
+  std::vector<LevelData> L;
+  std::shared_ptr<FabObj> phi0, rhs0;  // the caller's fabs (FP64)
+  OpTable resid0, rhsabs0, scale0, correct0, zero0_64;
+  DevBufP Mt, offr, offp, job;
+  int N = 0;
+  DevBufP dnorm;  // [0] residual norm bits, [1] rhs norm bits
+  unsigned long long* hnorm = nullptr;
+  cudaGraphExec_t step_graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  long long graph_kernels = 0;
+  ~Hierarchy() {
+    if (step_graph) cudaGraphExecDestroy(step_graph);
+    if (hnorm) cudaFreeHost(hnorm);
+  }
+};
+
+namespace {
+
+void build_tables(Ctx& c, Hierarchy& H, cudaStream_t s) {
+  const int nl = (int)H.L.size();
+  for (int l = 0; l < nl; ++l) {
+    LevelData& D = H.L[l];
+    const BoxArray& ba = D.bao->ba;
+    D.smooth = make_table(c, ba, 0, D.h, 0, [&](int b, DRow& R) {
+      R.v[0] = D.phi->view(b);
+      R.v[1] = D.rhs->view(b);
+    }, s);
+    D.zero = make_table(c, ba, 0, D.h, 0, [&](int b, DRow& R) { R.v[0] = D.phi->view(b); }, s);
+    if (D.fused) {
+      int per[3];
+      bc_code(&H.bc, per);
+      D.f_ab = make_fused(c, ba, D.h, *D.phi, *D.rhs, *D.phi2, per, 16, s);
+      D.f_ba = make_fused(c, ba, D.h, *D.phi2, *D.rhs, *D.phi, per, 16, s);
+      if (!D.f_ab.ok || !D.f_ba.ok) D.fused = false;
+    }
+    if (l + 1 < nl) {
+      const LevelData& C = H.L[l + 1];
+      D.rr = make_table(c, ba, 1, D.h, 0, [&](int b, DRow& R) {
+        R.v[0] = D.phi->view(b);
+        R.v[1] = D.rhs->view(b);
+        R.c[0] = coarse_view_of(*C.rhs, ba.boxes[b]);
+        R.c[1] = coarse_view_of(*C.phi, ba.boxes[b]);
+      }, s);
+      D.prolong = make_table(c, ba, 0, D.h, 0, [&](int b, DRow& R) {
+        R.v[0] = D.phi->view(b);
+        R.c[0] = coarse_view_of(*C.phi, ba.boxes[b]);
+      }, s);
+    }
+  }
+  // level-0 FP64 tables: norm check (and the mixed-precision scale / correction)
+  const BoxArray& ba0 = H.L[0].bao->ba;
+  const double h0 = H.L[0].h;
+  H.resid0 = make_table(c, ba0, 0, h0, 0, [&](int b, DRow& R) {
+    R.v[0] = H.phi0->view(b);
+    R.v[1] = H.rhs0->view(b);
+  }, s);
+  H.rhsabs0 = make_table(c, ba0, 0, h0, 1, [&](int b, DRow& R) { R.v[0] = H.rhs0->view(b); }, s);
+  H.zero0_64 = make_table(c, ba0, 0, h0, 0, [&](int b, DRow& R) { R.v[0] = H.phi0->view(b); }, s);
+  if (H.mixed) {
+    H.scale0 = make_table(c, ba0, 0, h0, 0, [&](int b, DRow& R) {
+      R.v[0] = H.phi0->view(b);
+      R.v[1] = H.rhs0->view(b);
+      R.c[0] = H.L[0].rhs->view(b);
+    }, s);
+    H.correct0 = make_table(c, ba0, 0, h0, 0, [&](int b, DRow& R) {
+      R.v[0] = H.phi0->view(b);
+      R.c[0] = H.L[0].phi->view(b);
+    }, s);
+  }
+  // bottom
+  const LevelData& B = H.L.back();
+  const BoxArray& bb = B.bao->ba;
+  int per[3];
+  bc_code(&H.bc, per);
+  int n[3] = {bb.dom.len(0), bb.dom.len(1), bb.dom.len(2)};
+  const std::vector<double>& Mt = bottom_matrix_t(c, n, per, B.h);
+  long long N = bb.dom.npts();
+  std::vector<long long> orhs(N), ophi(N);
+  for (size_t b = 0; b < bb.boxes.size(); ++b) {
+    const Box& X = bb.boxes[b];
+    for (int z = X.lo[2]; z <= X.hi[2]; ++z)
+      for (int y = X.lo[1]; y <= X.hi[1]; ++y)
+        for (int x = X.lo[0]; x <= X.hi[0]; ++x) {
+          long long i = ((long long)(z - bb.dom.lo[2]) * n[1] + (y - bb.dom.lo[1])) * n[0] +
+                        (x - bb.dom.lo[0]);
+          orhs[i] = B.rhs->lay.at(bb, (int)b, x, y, z);
+          ophi[i] = B.phi->lay.at(bb, (int)b, x, y, z);
+        }
+  }
+  H.N = (int)N;
+  H.Mt = c.upload(Mt.data(), Mt.size() * 8, s);
+  H.offr = c.upload(orhs.data(), N * 8, s);
+  H.offp = c.upload(ophi.data(), N * 8, s);
+  BottomJob J{};
+  J.Mt = (const double*)H.Mt->p;
+  J.off_rhs = (const long long*)H.offr->p;
+  J.off_phi = (const long long*)H.offp->p;
+  J.rhs = B.rhs->base;
+  J.phi = B.phi->base;
+  J.N = (int)N;
+  H.job = c.upload(&J, sizeof J, s);
+  // fill plans must exist before any graph capture
+  for (auto& D : H.L) {
+    fill_plan(c, *D.phi, &H.bc);
+    if (D.fused) {
+      fill_plan(c, *D.phi2, &H.bc);
+      fill_plan(c, *D.rhs, &H.bc);
+    }
+  }
+  fill_plan(c, *H.phi0, &H.bc);
+}
+
+Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, const SolveParams& p) {
+  int per[3];
+  int key = bc_code(bc, per);
+  for (auto& h : c.hier) {
+    if (h->rhs_id == rhs.id && h->phi_id == phi.id && h->bc_key == key &&
+        h->p.nu1 == p.nu1 && h->p.nu2 == p.nu2 && h->p.precision == p.precision &&
+        h->p.smoother == p.smoother && h->p.h == p.h)
+      return *h;
+  }
+  if (rhs.dtype != DT_F64 || phi.dtype != DT_F64) fail(MG_EINVAL, "mg_solve needs FP64 fabs");
+  if (rhs.lay.ncomp != 1 || phi.lay.ncomp != 1) fail(MG_EINVAL, "mg_solve needs 1-component fabs");
+  if (!same_boxes(rhs.ba->ba, phi.ba->ba)) fail(MG_EINVAL, "rhs and phi are on different box arrays");
+  if (phi.lay.g < 1) fail(MG_EINVAL, "phi needs at least one ghost cell");
+  const std::vector<BoxArray>& lev = phi.ba->hierarchy();
+  for (size_t l = 0; l + 1 < lev.size(); ++l)
+    if (!aligned(lev[l]))
+      fail(MG_EINVAL, "box array not supported by the solver: a level has boxes with odd bounds");
+  std::unique_ptr<Hierarchy> H(new Hierarchy);
+  H->rhs_id = rhs.id;
+  H->phi_id = phi.id;
+  H->bc_key = key;
+  H->p = p;
+  H->bc = *bc;
+  H->mixed = p.precision == MG_PREC_MIXED;
+  H->dt = H->mixed ? DT_F32 : DT_F64;
+  H->phi0 = c.get_fab(phi.id);
+  H->rhs0 = c.get_fab(rhs.id);
+  cudaStream_t s = c.stream;
+  const int nl = (int)lev.size();
+  H->L.resize(nl);
+  double h = p.h;
+  for (int l = 0; l < nl; ++l) {
+    LevelData& D = H->L[l];
+    D.h = h;
+    h *= 2.0;
+    if (l == 0) D.bao = phi.ba;
+    else {
+      D.bao = std::make_shared<BoxArrayObj>();
+      D.bao->ba = lev[l];
+    }
+    const bool want_fused = p.smoother != MG_SMOOTH_HALF && l + 1 < nl;
+    if (l == 0 && !H->mixed) {
+      D.phi = H->phi0;
+      D.rhs = H->rhs0;
+      D.fused = want_fused && fused_eligible(*D.phi, *D.rhs);
+      if (p.smoother == MG_SMOOTH_FUSED && want_fused && !D.fused)
+        fail(MG_EINVAL, "fused smoother needs phi nghost >= 2 and rhs nghost >= 1");
+    } else {
+      D.phi = internal_fab(c, D.bao, want_fused ? 2 : 1, H->dt);
+      D.rhs = internal_fab(c, D.bao, want_fused ? 1 : 0, H->dt);
+      D.fused = want_fused;
+    }
+    if (D.fused) D.phi2 = internal_fab(c, D.bao, D.phi->lay.g, H->dt);
+  }
+  build_tables(c, *H, s);
+  H->dnorm = c.alloc(16, s);
+  MG_CK(cudaMallocHost(&H->hnorm, 16));
+  MG_CK(cudaStreamSynchronize(s));
+  c.hier.push_back(std::move(H));
+  return *c.hier.back();
+}
+
+void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s) {
+  int k = 0;
+  if (D.fused) {
+    // pairs of fused sweeps: phi -> phi2 -> phi
+    for (; k + 1 < sweeps; k += 2) {
+      launch_fill(c, *D.phi, &H.bc, s);
+      launch_fused(c, D.f_ab, H.dt, s);
+      launch_fill(c, *D.phi2, &H.bc, s);
+      launch_fused(c, D.f_ba, H.dt, s);
+    }
+  }
+  for (; k < sweeps; ++k)
+    for (int color = 0; color < 2; ++color) {
+      launch_fill(c, *D.phi, &H.bc, s);
+      MG_CK(launch_rbgs_half(H.dt, D.smooth.rows(), D.smooth.nbox, D.smooth.nrows, color, s));
+    }
+}
+
+void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s) {
+  const int nl = (int)H.L.size();
+  for (int l = 0; l + 1 < nl; ++l) {
+    LevelData& D = H.L[l];
+    if (D.fused) launch_fill(c, *D.rhs, &H.bc, s);  // rhs ghosts for the redundant ring
+    smooth(c, H, D, H.p.nu1, s);
+    launch_fill(c, *D.phi, &H.bc, s);
+    MG_CK(launch_residual_restrict(H.dt, D.rr.rows(), D.rr.nbox, D.rr.nrows, s));
+  }
+  MG_CK(launch_bottom(H.dt, (const BottomJob*)H.job->p, 1, H.N, s));
+  for (int l = nl - 2; l >= 0; --l) {
+    LevelData& D = H.L[l];
+    MG_CK(launch_prolong_add(H.dt, D.prolong.rows(), D.prolong.nbox, D.prolong.nrows, s));
+    smooth(c, H, D, H.p.nu2, s);
+  }
+}
+
+// One outer iteration: the cycle (with the mixed-precision scale / correction around it),
+// then the norm check of the new iterate.
+void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
+  unsigned long long* dn = (unsigned long long*)H.dnorm->p;
+  if (H.mixed) {
+    MG_CK(launch_residual_scale_f32(H.scale0.rows(), H.scale0.nbox, H.scale0.nrows, dn, s));
+    LevelData& D0 = H.L[0];
+    MG_CK(launch_set_valid(DT_F32, D0.zero.rows(), D0.zero.nbox, D0.zero.nrows, 0.0, s));
+  }
+  enqueue_vcycle(c, H, s);
+  if (H.mixed)
+    MG_CK(launch_correct_add(H.correct0.rows(), H.correct0.nbox, H.correct0.nrows, dn, s));
+  MG_CK(cudaMemsetAsync(dn, 0, 8, s));
+  launch_fill(c, *H.phi0, &H.bc, s);
+  MG_CK(launch_residual(DT_F64, H.resid0.rows(), H.resid0.nbox, H.resid0.nrows, dn, s));
+  MG_CK(cudaMemcpyAsync(H.hnorm, dn, 16, cudaMemcpyDeviceToHost, s));
+}
+
+void run_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
+  bool graph = H.p.use_graph && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+  if (graph && H.step_graph && H.graph_stream != s) {
+    cudaGraphExecDestroy(H.step_graph);
+    H.step_graph = nullptr;
+  }
+  if (graph && !H.step_graph) {
+    cudaGraph_t g = nullptr;
+    const long long before = launches_so_far();
+    MG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue_step(c, H, s);
+    } catch (...) {
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      count_launches(before - launches_so_far());
+      throw;
+    }
+    MG_CK(cudaStreamEndCapture(s, &g));
+    H.graph_kernels = launches_so_far() - before;  // captured, not executed
+    count_launches(-H.graph_kernels);
+    cudaError_t e = cudaGraphInstantiate(&H.step_graph, g, 0);
+    cudaGraphDestroy(g);
+    MG_CK(e);
+    H.graph_stream = s;
+  }
+  if (graph) {
+    MG_CK(cudaGraphLaunch(H.step_graph, s));
+    count_launches(H.graph_kernels);
+  } else {
+    enqueue_step(c, H, s);
+  }
+}
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  std::memcpy(&d, &b, 8);
+  return d;
+}
+
+}  // namespace
+
+void drop_hierarchies_of(Ctx& c, int64_t fab_id) {
+  bool any = false;
+  for (auto& h : c.hier)
+    if (h->rhs_id == fab_id || h->phi_id == fab_id) any = true;
+  if (!any) return;
+  cudaStreamSynchronize(c.stream);
+  std::vector<std::shared_ptr<Hierarchy>> keep;
+  for (auto& h : c.hier)
+    if (h->rhs_id != fab_id && h->phi_id != fab_id) keep.push_back(std::move(h));
+  c.hier.swap(keep);
+}
+
+void destroy_hierarchies(Ctx& c) { c.hier.clear(); }
+
+int solve(Ctx& c, int64_t rhs_id, int64_t phi_id, const mg_bc* bc, double tol,
+          const SolveParams& p, mg_result* res) {
+  c.require_device();
+  if (!(tol >= 0)) fail(MG_EINVAL, "tol must be >= 0");
+  auto rhs = c.get_fab(rhs_id);
+  auto phi = c.get_fab(phi_id);
+  double t_start = c.now();
+  Hierarchy& H = get_hierarchy(c, *rhs, *phi, bc, p);
+  cudaStream_t s = c.stream;
+  unsigned long long* dn = (unsigned long long*)H.dnorm->p;
+  // ||rhs||_inf and the first residual norm
+  MG_CK(cudaMemsetAsync(dn, 0, 16, s));
+  MG_CK(launch_maxabs(DT_F64, H.rhsabs0.rows(), H.rhsabs0.nbox, H.rhsabs0.nrows, dn, s));
+  launch_fill(c, *H.phi0, bc, s);
+  MG_CK(launch_residual(DT_F64, H.resid0.rows(), H.resid0.nbox, H.resid0.nrows, dn, s));
+  MG_CK(cudaMemcpyAsync(H.hnorm, dn, 16, cudaMemcpyDeviceToHost, s));
+  MG_CK(cudaStreamSynchronize(s));
+  const double rhsnorm = bits_to_double(H.hnorm[1]);
+  mg_result r{};
+  r.t_start = t_start;
+  int status = MG_OK;
+  int it = 0;
+  double rn = bits_to_double(H.hnorm[0]);
+  if (std::isnan(rhsnorm) || std::isinf(rhsnorm)) {
+    status = MG_ENAN;
+  } else if (rhsnorm == 0.0) {
+    MG_CK(launch_set_valid(DT_F64, H.zero0_64.rows(), H.zero0_64.nbox, H.zero0_64.nrows, 0.0, s));
+    MG_CK(cudaStreamSynchronize(s));
+    rn = 0.0;
+  } else {
+    for (;;) {
+      if (std::isnan(rn) || std::isinf(rn)) { status = MG_ENAN; break; }
+      if (p.fixed_vcycles >= 0) {
+        if (it == p.fixed_vcycles) break;
+      } else {
+        if (rn <= tol * rhsnorm) break;
+        if (it == p.max_iter) { status = MG_NOT_CONVERGED; break; }
+      }
+      run_step(c, H, s);
+      MG_CK(cudaStreamSynchronize(s));
+      rn = bits_to_double(H.hnorm[0]);
+      ++it;
+    }
+  }
+  check_device_error(c);
+  r.status = status;
+  r.vcycles = it;
+  r.rel_resid = rhsnorm > 0 ? rn / rhsnorm : 0.0;
+  r.t_end = c.now();
+  r.seconds = r.t_end - t_start;
+  if (res) *res = r;
+  return status;
+}
+
+int solve_batch(Ctx& c, int n, const int64_t* rhs, const int64_t* phi, const mg_bc* bcs,
+                double tol, const SolveParams& p, mg_result* res) {
+  (void)c; (void)n; (void)rhs; (void)phi; (void)bcs; (void)tol; (void)p; (void)res;
+  fail(MG_EINVAL, "batched solve not built yet");
+}
+
+int server_submit(Ctx& c, int64_t rhs, int64_t phi, const mg_bc* bc, double tol,
+                  const SolveParams& p, int64_t* ticket) {
+  (void)c; (void)rhs; (void)phi; (void)bc; (void)tol; (void)p; (void)ticket;
+  fail(MG_EINVAL, "serving not built yet");
+}
+
+int server_poll(Ctx& c, int64_t ticket, int timeout_ms, mg_result* res) {
+  (void)c; (void)ticket; (void)timeout_ms; (void)res;
+  fail(MG_EINVAL, "serving not built yet");
+}
+
+void server_stop(Ctx& c) { (void)c; }
+
+}  // namespace gbmg
+
+using namespace gbmg;
+
+extern "C" {
+
+int mg_solve(mg_ctx_t h, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, double tol,
+             const mg_options* opt, mg_result* res) {
+  return guard([&] {
+    Ctx* c = (Ctx*)h;
+    if (!c) fail(MG_EINVAL, "ctx is NULL");
+    auto f = c->get_fab(phi);
+    SolveParams p = params_from(opt, f->ba->ba);
+    return solve(*c, rhs, phi, bc, tol, p, res);
+  });
+}
+
+int mg_solve_batch(mg_ctx_t h, int n, const mg_fab_t* rhs, const mg_fab_t* phi, const mg_bc* bcs,
+                   double tol, const mg_options* opt, mg_result* res) {
+  return guard([&] {
+    Ctx* c = (Ctx*)h;
+    if (!c || n <= 0 || !rhs || !phi || !bcs) fail(MG_EINVAL, "bad argument");
+    auto f = c->get_fab(phi[0]);
+    SolveParams p = params_from(opt, f->ba->ba);
+    return solve_batch(*c, n, rhs, phi, bcs, tol, p, res);
+  });
+}
+
+int mg_submit(mg_ctx_t h, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, double tol,
+              const mg_options* opt, mg_ticket_t* out) {
+  return guard([&] {
+    Ctx* c = (Ctx*)h;
+    if (!c || !out) fail(MG_EINVAL, "bad argument");
+    auto f = c->get_fab(phi);
+    SolveParams p = params_from(opt, f->ba->ba);
+    return server_submit(*c, rhs, phi, bc, tol, p, out);
+  });
+}
+
+int mg_poll(mg_ctx_t h, mg_ticket_t ticket, int timeout_ms, mg_result* res) {
+  return guard([&] {
+    Ctx* c = (Ctx*)h;
+    if (!c) fail(MG_EINVAL, "ctx is NULL");
+    return server_poll(*c, ticket, timeout_ms, res);
+  });
+}
+
+}  // extern "C"

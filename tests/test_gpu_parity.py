@@ -1,0 +1,356 @@
+"""GPU parity: every kernel of the path, called through the C ABI, against the CPU oracle on
+the same seeded inputs; then whole solves.  Ghost fill and box bookkeeping are compared
+bit for bit; the FP64 stencil kernels are written so that each operation is one IEEE
+rounding in the oracle's order, so they are compared bit for bit as well; whole solves
+differ from the oracle only through the independently computed bottom matrix and are held
+to 1e-12 relative."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_12179_gb300 import inputs, mg
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+Z3 = (0, 0, 0)
+
+
+@pytest.fixture(scope="module")
+def gctx():
+    import paper_2403_12179_gb300.build as b
+    b.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.init()
+    ctx = mg.mg_init(0)
+    yield ctx
+    mg.mg_finalize(ctx)
+
+
+def _ba(ctx, dom, mb):
+    ba = mg.mg_box_array_create(ctx, Z3, dom, mb)
+    return ba, mg.mg_box_array_info(ctx, ba)[1]
+
+
+FILL_CASES = [((11, 9, 7), (5, 4, 8), 2, 2), ((31, 31, 31), (16, 16, 16), 2, 4),
+              ((15, 15, 15), (8, 8, 8), 1, 1), ((3, 3, 3), (4, 4, 4), 2, 1),
+              ((23, 15, 7), (8, 8, 8), 1, 3)]
+
+
+@pytest.mark.parametrize("dom,mb,ng,ncomp", FILL_CASES)
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (1, 0, 1)])
+@pytest.mark.parametrize("dt", [mg.MG_F64, mg.MG_F32])
+def test_fill_boundary_bitwise(gctx, orc, dom, mb, ng, ncomp, periodic, dt):
+    ba, boxes = _ba(gctx, dom, mb)
+    npdt = np.float64 if dt == mg.MG_F64 else np.float32
+    g = inputs.rng(31)
+    fabs = [g.standard_normal(f.shape).astype(npdt) for f in orc.new_field(boxes, ng, ncomp)]
+    ref = orc.fill_boundary(Z3, dom, periodic, boxes, fabs, ng)
+    fab = gu.to_fab(gctx, ba, fabs, ng, dt)
+    mg.mg_fill_boundary(gctx, fab, mg.make_bc(periodic))
+    got = gu.from_fab(gctx, fab, len(boxes))
+    for a, r in zip(got, ref):
+        assert np.array_equal(a, r)
+    mg.mg_fab_free(gctx, fab)
+
+
+def _level_inputs(orc, boxes, dom, periodic, ng_phi, ng_rhs, seed, dt=np.float64):
+    g = inputs.rng(seed)
+    phi = [g.standard_normal(f.shape).astype(dt) for f in orc.new_field(boxes, ng_phi)]
+    rhs = [g.standard_normal(f.shape).astype(dt) for f in orc.new_field(boxes, ng_rhs)]
+    phi = orc.fill_boundary(Z3, dom, periodic, boxes, phi, ng_phi)
+    return phi, rhs
+
+
+@pytest.mark.parametrize("color", [0, 1])
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (0, 1, 0)])
+@pytest.mark.parametrize("dt", [mg.MG_F64, mg.MG_F32])
+def test_rbgs_half_sweep_bitwise(gctx, orc, color, periodic, dt):
+    dom, mb, h = (19, 15, 11), (8, 8, 6), 1.0 / 20
+    npdt = np.float64 if dt == mg.MG_F64 else np.float32
+    ba, boxes = _ba(gctx, dom, mb)
+    phi, rhs = _level_inputs(orc, boxes, dom, periodic, 1, 0, 32, npdt)
+    ref = orc.rbgs(Z3, dom, boxes, h, phi, 1, rhs, 0, color)
+    fp, fr = gu.to_fab(gctx, ba, phi, 1, dt), gu.to_fab(gctx, ba, rhs, 0, dt)
+    mg.mg_smooth(gctx, fp, fr, mg.make_bc(periodic), h, color)
+    got = gu.from_fab(gctx, fp, len(boxes))
+    for a, r in zip(got, ref):
+        assert np.array_equal(gu.valid(a, 1), gu.valid(r, 1))
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 1)])
+def test_full_sweep_matches_fill_red_fill_black(gctx, orc, periodic):
+    dom, mb, h = (15, 15, 15), (8, 8, 8), 1.0 / 16
+    ba, boxes = _ba(gctx, dom, mb)
+    phi, rhs = _level_inputs(orc, boxes, dom, periodic, 2, 1, 33)
+    ref = phi
+    for color in (0, 1):
+        ref = orc.fill_boundary(Z3, dom, periodic, boxes, ref, 2)
+        ref = orc.rbgs(Z3, dom, boxes, h, ref, 2, rhs, 1, color)
+    fp, fr = gu.to_fab(gctx, ba, phi, 2), gu.to_fab(gctx, ba, rhs, 1)
+    mg.mg_smooth(gctx, fp, fr, mg.make_bc(periodic), h, 2)
+    got = gu.from_fab(gctx, fp, len(boxes))
+    for a, r in zip(got, ref):
+        assert np.array_equal(gu.valid(a, 2), gu.valid(r, 2))
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0)])
+def test_residual_and_norm_bitwise(gctx, orc, periodic):
+    dom, mb, h = (23, 15, 31), (8, 16, 12), 1.0 / 24
+    ba, boxes = _ba(gctx, dom, mb)
+    phi, rhs = _level_inputs(orc, boxes, dom, periodic, 1, 0, 34)
+    r_ref, n_ref = orc.residual(Z3, dom, boxes, h, phi, 1, rhs, 0)
+    fp, fr = gu.to_fab(gctx, ba, phi, 1), gu.to_fab(gctx, ba, rhs, 0)
+    fo = mg.mg_fab_alloc(gctx, ba, 1, 0)
+    nrm = mg.mg_residual(gctx, fp, fr, fo, h)
+    got = gu.from_fab(gctx, fo, len(boxes))
+    for a, r in zip(got, r_ref):
+        assert np.array_equal(a, r)
+    assert nrm == n_ref
+
+
+@pytest.mark.parametrize("dom,mb", [((31, 31, 31), (16, 16, 16)), ((15, 15, 15), (4, 4, 4)),
+                                    ((47, 23, 15), (32, 16, 8))])
+def test_residual_restrict_bitwise(gctx, orc, dom, mb):
+    h = 1.0 / (dom[0] + 1)
+    periodic = (1, 0, 1)
+    ba, boxes = _ba(gctx, dom, mb)
+    levels = orc.hierarchy(Z3, dom, boxes)
+    cba = mg.mg_hierarchy_level(gctx, ba, 1)
+    cboxes = mg.mg_box_array_info(gctx, cba)[1]
+    assert np.array_equal(np.array(cboxes), levels[1][2])
+    phi, rhs = _level_inputs(orc, boxes, dom, periodic, 1, 0, 35)
+    r, _ = orc.residual(Z3, dom, boxes, h, phi, 1, rhs, 0)
+    c_ref = orc.restrict(levels[0], r, 0, levels[1], 0)
+    fp, fr = gu.to_fab(gctx, ba, phi, 1), gu.to_fab(gctx, ba, rhs, 0)
+    crhs = mg.mg_fab_alloc(gctx, cba, 1, 0)
+    cphi = mg.mg_fab_alloc(gctx, cba, 1, 1)
+    mg.mg_fab_set_val(gctx, cphi, 7.0)
+    mg.mg_residual_restrict(gctx, fp, fr, crhs, cphi, h)
+    got = gu.from_fab(gctx, crhs, len(cboxes))
+    for a, c in zip(got, c_ref):
+        assert np.array_equal(a, c)
+    for a in gu.from_fab(gctx, cphi, len(cboxes)):
+        assert not gu.valid(a, 1).any()
+
+
+def test_restrict_and_prolong_bitwise(gctx, orc):
+    dom, mb = (31, 15, 23), (8, 8, 8)
+    ba, boxes = _ba(gctx, dom, mb)
+    levels = orc.hierarchy(Z3, dom, boxes)
+    cba = mg.mg_hierarchy_level(gctx, ba, 1)
+    cboxes = mg.mg_box_array_info(gctx, cba)[1]
+    g = inputs.rng(36)
+    fine = [g.standard_normal(f.shape) for f in orc.new_field(boxes, 1)]
+    coarse = [g.standard_normal(f.shape) for f in orc.new_field(cboxes, 1)]
+    ff, fc = gu.to_fab(gctx, ba, fine, 1), gu.to_fab(gctx, cba, coarse, 1)
+    mg.mg_restrict(gctx, ff, fc)
+    c_ref = orc.restrict(levels[0], fine, 1, levels[1], 1)
+    for a, c in zip(gu.from_fab(gctx, fc, len(cboxes)), c_ref):
+        assert np.array_equal(gu.valid(a, 1), gu.valid(c, 1))
+    fc2 = gu.to_fab(gctx, cba, coarse, 1)
+    mg.mg_prolong_add(gctx, fc2, ff)
+    p_ref = orc.prolong_add(levels[1], coarse, 1, levels[0], fine, 1)
+    for a, p in zip(gu.from_fab(gctx, ff, len(boxes)), p_ref):
+        assert np.array_equal(gu.valid(a, 1), gu.valid(p, 1))
+
+
+@pytest.mark.parametrize("n,mb", [((2, 2, 2), (2, 2, 2)), ((3, 3, 3), (3, 3, 3)),
+                                  ((4, 6, 2), (2, 3, 2)), ((8, 8, 8), (4, 8, 8))])
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (0, 1, 0)])
+def test_bottom_solve(gctx, orc, n, mb, periodic):
+    dom = tuple(v - 1 for v in n)
+    h = 0.25
+    ba, boxes = _ba(gctx, dom, mb)
+    g = inputs.rng(37)
+    rhs = g.standard_normal((n[2], n[1], n[0]))
+    M = orc.bottom_matrix(n, periodic, h)
+    ref = (M @ rhs.ravel()).reshape(rhs.shape)
+    fr = gu.dense_fab(gctx, ba, rhs, 0)
+    fp = mg.mg_fab_alloc(gctx, ba, 1, 1)
+    mg.mg_bottom_solve(gctx, fr, fp, mg.make_bc(periodic), h)
+    got = gu.fab_dense(gctx, fp, rhs.shape)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_dense_roundtrip_and_set_val(gctx):
+    dom = (20, 13, 9)
+    ba, boxes = _ba(gctx, dom, (8, 8, 8))
+    x = inputs.rng(38).standard_normal((3, 10, 14, 21))
+    fab = mg.mg_fab_alloc(gctx, ba, 3, 2)
+    t = torch.from_numpy(x).pin_memory()
+    mg.mg_fab_copy_from_dense(gctx, fab, t.data_ptr(), True)
+    out = torch.empty_like(t).pin_memory()
+    mg.mg_fab_copy_to_dense(gctx, fab, out.data_ptr(), True)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.numpy(), x)
+    mg.mg_fab_set_val(gctx, fab, 2.5, include_ghosts=False)
+    for a in gu.from_fab(gctx, fab, len(boxes)):
+        assert np.all(gu.valid(a, 2) == 2.5)
+        assert np.all(a[:, 0] == 0.0)
+
+
+# ---- whole solves ----------------------------------------------------------------------
+
+def _solve_pair(gctx, orc, n, mb, periodic, rhs, tol=1e-10, fixed=-1, precision=mg.MG_PREC_F64,
+                use_graph=1, ng=(1, 0)):
+    dom = (n - 1,) * 3
+    h = 1.0 / n
+    ba, boxes = _ba(gctx, dom, mb)
+    fr = gu.dense_fab(gctx, ba, rhs, ng[1])
+    fp = mg.mg_fab_alloc(gctx, ba, 1, ng[0])
+    opt = mg.make_options(fixed_vcycles=fixed, precision=precision, use_graph=use_graph)
+    res = mg.mg_solve(gctx, fr, fp, mg.make_bc(periodic), tol, opt)
+    phi = gu.fab_dense(gctx, fp, rhs.shape)
+    mg.mg_fab_free(gctx, fr)
+    mg.mg_fab_free(gctx, fp)
+    return phi, res
+
+
+def test_periodic_sine_64_matches_oracle(gctx, orc):
+    n = 64
+    rhs = inputs.periodic_sine(n, seed=1)
+    phi, res = _solve_pair(gctx, orc, n, (32, 32, 32), (1, 1, 1), rhs)
+    o_phi, st, vc, hist = orc.solve(Z3, (63,) * 3, (1, 1, 1), orc.chop(Z3, (63,) * 3, (32,) * 3),
+                                    1.0 / n, rhs)
+    assert res.status == mg.MG_OK and st == 0
+    assert res.vcycles == vc
+    assert res.rel_resid <= 1e-10 and abs(res.rel_resid - hist[-1]) <= 1e-3 * hist[-1]
+    assert np.abs(phi - o_phi).max() <= 1e-12 * np.abs(o_phi).max()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0)])
+def test_iterates_match_oracle(gctx, orc, k, periodic):
+    n = 32
+    rhs = inputs.rng(40).standard_normal((n, n, n))
+    if all(periodic):
+        rhs = inputs.remove_mean(rhs)
+    phi, res = _solve_pair(gctx, orc, n, (16, 16, 16), periodic, rhs, fixed=k)
+    o_phi, _, vc, hist = orc.solve(Z3, (n - 1,) * 3, periodic, orc.chop(Z3, (n - 1,) * 3, (16,) * 3),
+                                   1.0 / n, rhs, fixed_vcycles=k)
+    assert res.vcycles == k == vc
+    assert np.abs(phi - o_phi).max() <= 1e-12 * np.abs(o_phi).max()
+
+
+def test_decomposition_invariance_bitwise(gctx, orc):
+    n = 32
+    rhs = inputs.rng(41).standard_normal((n, n, n))
+    ref = None
+    for mb in [(32, 32, 32), (16, 16, 16), (8, 8, 8), (16, 8, 32)]:
+        phi, res = _solve_pair(gctx, orc, n, mb, (0, 0, 0), rhs, fixed=3)
+        if ref is None:
+            ref = phi
+        assert np.array_equal(phi, ref)
+
+
+def test_graph_replay_matches_eager(gctx, orc):
+    n = 32
+    rhs = inputs.rng(42).standard_normal((n, n, n))
+    a, ra = _solve_pair(gctx, orc, n, (16, 16, 16), (0, 1, 0), rhs, use_graph=1)
+    b, rb = _solve_pair(gctx, orc, n, (16, 16, 16), (0, 1, 0), rhs, use_graph=0)
+    assert ra.vcycles == rb.vcycles and np.array_equal(a, b)
+
+
+def test_edge_cases(gctx, orc):
+    # zero rhs gives phi = 0 in zero V-cycles
+    phi, res = _solve_pair(gctx, orc, 8, (4, 4, 4), (1, 1, 1), np.zeros((8, 8, 8)))
+    assert res.status == mg.MG_OK and res.vcycles == 0 and not phi.any()
+    # NaN in rhs is reported
+    rhs = np.ones((8, 8, 8))
+    rhs[1, 2, 3] = np.nan
+    _, res = _solve_pair(gctx, orc, 8, (4, 4, 4), (0, 0, 0), rhs)
+    assert res.status == mg.MG_ENAN
+    # domain that is its own bottom level: exact in one cycle
+    rhs = inputs.rng(43).standard_normal((2, 2, 2))
+    phi, res = _solve_pair(gctx, orc, 2, (2, 2, 2), (0, 0, 0), rhs)
+    o_phi, _, vc, _ = orc.solve(Z3, (1, 1, 1), (0, 0, 0), orc.chop(Z3, (1, 1, 1), (2, 2, 2)), 0.5, rhs)
+    assert res.status == mg.MG_OK and res.vcycles == vc == 1
+    assert np.abs(phi - o_phi).max() <= 1e-13 * np.abs(o_phi).max()
+    # max_iter reached
+    rhs = inputs.rng(44).standard_normal((16, 16, 16))
+    dom = (15, 15, 15)
+    ba, _ = _ba(gctx, dom, (8, 8, 8))
+    fr, fp = gu.dense_fab(gctx, ba, rhs, 0), mg.mg_fab_alloc(gctx, ba, 1, 1)
+    res = mg.mg_solve(gctx, fr, fp, mg.make_bc((0, 0, 0)), 1e-10, mg.make_options(max_iter=2))
+    assert res.status == mg.MG_NOT_CONVERGED and res.vcycles == 2
+
+
+def test_mixed_precision_solve(gctx, orc):
+    n = 64
+    rhs = inputs.gaussian_blobs(n, seed=5)
+    tol = 1e-10
+    p64, r64 = _solve_pair(gctx, orc, n, (32, 32, 32), (0, 0, 0), rhs, tol=tol)
+    pmx, rmx = _solve_pair(gctx, orc, n, (32, 32, 32), (0, 0, 0), rhs, tol=tol,
+                           precision=mg.MG_PREC_MIXED)
+    assert r64.status == mg.MG_OK and rmx.status == mg.MG_OK and rmx.rel_resid <= tol
+    assert np.abs(pmx - p64).max() <= 2 * 0.06 * tol * np.abs(rhs).max()
+    o_phi, st, vc, _ = orc.solve(Z3, (n - 1,) * 3, (0, 0, 0), orc.chop(Z3, (n - 1,) * 3, (32,) * 3),
+                                 1.0 / n, rhs, tol=tol, mixed=True)
+    assert st == 0 and abs(rmx.vcycles - vc) <= 1
+    assert np.abs(pmx - o_phi).max() <= 2 * 0.06 * tol * np.abs(rhs).max()
+
+
+def test_full_size_dirichlet_256(gctx, orc):
+    """The benchmarked workload: 256^3 Dirichlet, 64 boxes of 64^3, Jacobi-smoothed N(0,1)."""
+    n = 256
+    rhs = inputs.dirichlet_jacobi(n, seed=2)
+    phi, res = _solve_pair(gctx, orc, n, (64, 64, 64), (0, 0, 0), rhs, ng=(2, 1))
+    assert res.status == mg.MG_OK and res.rel_resid <= 1e-10 and res.vcycles <= 30
+    r = gu.residual_numpy(phi, rhs, (0, 0, 0), 1.0 / n)
+    assert np.abs(r).max() <= 1.01e-10 * np.abs(rhs).max()
+    o_phi, st, vc, hist = orc.solve(Z3, (n - 1,) * 3, (0, 0, 0), orc.chop(Z3, (n - 1,) * 3, (64,) * 3),
+                                    1.0 / n, rhs)
+    assert st == 0 and res.vcycles == vc
+    assert np.abs(phi - o_phi).max() <= 1e-12 * np.abs(o_phi).max()
+
+
+# ---- fused red + black sweep (TMA-staged z-slabs) ---------------------------------------
+
+FUSED_CASES = [((63, 63, 63), (64, 64, 64)), ((47, 37, 21), (24, 19, 11)), ((15, 15, 15), (4, 4, 4)),
+               ((31, 31, 31), (16, 16, 16)), ((7, 9, 5), (3, 5, 6))]
+
+
+@pytest.mark.parametrize("dom,mb", FUSED_CASES)
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (1, 0, 0), (0, 1, 1)])
+@pytest.mark.parametrize("dt", [mg.MG_F64, mg.MG_F32])
+def test_fused_sweep_bitwise(gctx, orc, dom, mb, periodic, dt):
+    npdt = np.float64 if dt == mg.MG_F64 else np.float32
+    h = 1.0 / (dom[0] + 1)
+    ba, boxes = _ba(gctx, dom, mb)
+    g = inputs.rng(45)
+    phi = [g.standard_normal(f.shape).astype(npdt) for f in orc.new_field(boxes, 2)]
+    rhs = [g.standard_normal(f.shape).astype(npdt) for f in orc.new_field(boxes, 1)]
+    ref = phi
+    for color in (0, 1):
+        ref = orc.fill_boundary(Z3, dom, periodic, boxes, ref, 2)
+        ref = orc.rbgs(Z3, dom, boxes, h, ref, 2, rhs, 1, color)
+    bc = mg.make_bc(periodic)
+    fa, fr = gu.to_fab(gctx, ba, phi, 2, dt), gu.to_fab(gctx, ba, rhs, 1, dt)
+    fb = mg.mg_fab_alloc(gctx, ba, 1, 2, dt)
+    mg.mg_fill_boundary(gctx, fa, bc)
+    mg.mg_fill_boundary(gctx, fr, bc)
+    mg.mg_smooth_fused(gctx, fa, fr, fb, bc, h)
+    got = gu.from_fab(gctx, fb, len(boxes))
+    for a, r in zip(got, ref):
+        assert np.array_equal(gu.valid(a, 2), gu.valid(r, 2))
+    for f in (fa, fr, fb):
+        mg.mg_fab_free(gctx, f)
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0)])
+def test_fused_solver_equals_half_sweep_solver(gctx, orc, periodic):
+    n = 64
+    rhs = inputs.rng(46).standard_normal((n, n, n))
+    if all(periodic):
+        rhs = inputs.remove_mean(rhs)
+    dom = (n - 1,) * 3
+    out = []
+    for sm in (mg.MG_SMOOTH_FUSED, mg.MG_SMOOTH_HALF):
+        ba, _ = _ba(gctx, dom, (32, 32, 32))
+        fr = gu.dense_fab(gctx, ba, rhs, 1)
+        fp = mg.mg_fab_alloc(gctx, ba, 1, 2)
+        res = mg.mg_solve(gctx, fr, fp, mg.make_bc(periodic), 1e-10, mg.make_options(smoother=sm))
+        out.append((gu.fab_dense(gctx, fp, rhs.shape), res.vcycles, res.status))
+    assert out[0][2] == out[1][2] == mg.MG_OK and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
