@@ -13,16 +13,18 @@
 //       - homogeneous Dirichlet faces: ghost = -(mirror cell across the face); a ghost cell
 //         outside the domain in two or more non-periodic directions is 0
 //       - red-black Gauss-Seidel, colour (i+j+k) mod 2 on global indices, red (0) first,
-//         ghost fill before each colour, sum order x-,x+,y-,y+,z-,z+
-//       - residual r = rhs - (s - 6 phi) * (1/h^2), max-norm
+//         ghost fill before each colour, sum order x-,x+,y-,y+,z-,z+; the update is
+//         phi = fma(-h^2, rhs, s) * (1/6) with 1/6 rounded once
+//       - residual r = fma(-1/h^2, fma(-6, phi, s), rhs), max-norm
 //       - restriction = mean of the 8 children (x fastest sum order), coarse guess 0,
 //         coarse operator rediscretised with h_{l+1} = 2 h_l
 //       - prolongation = piecewise-constant injection added to phi
 //       - bottom = exact solve by the closed-form (pseudo-)inverse built from the discrete
 //         sine / Fourier eigenvectors of the 1-D operators
 //       - V(nu1, nu2) cycle, stop when ||rhs - A phi||_inf <= tol ||rhs||_inf
-//       - mixed form: FP64 outer residual / correction, FP32 inner V-cycle on r / ||r||_inf,
-//         FP64 bottom
+//       - mixed form: FP64 outer residual / correction, FP32 inner V-cycle on r * 2^-e with
+//         2^e <= ||r||_inf < 2^(e+1) (an exact rescaling), FP64 bottom,
+//         phi = fma(2^e, e_inner, phi)
 //   * Parity of these functions is pinned by mathematics, not by the paper: closed-form
 //     eigenvalues, a dense brute-force solve, transfer identities, decomposition
 //     invariance and second-order convergence (tests/test_oracle_pins.py).
@@ -189,11 +191,13 @@ inline R nbr_sum(const Field<R>& f, int b, int x, int y, int z) {
 }
 
 // One red-black Gauss-Seidel half-sweep of colour `color` (0 = red): every cell with
-// (x+y+z) mod 2 == color takes phi = (s - h^2 rhs) / 6.  phi's ghosts must be filled.
+// (x+y+z) mod 2 == color takes phi = (s - h^2 rhs) / 6, evaluated as
+// fma(-h^2, rhs, s) * (1/6).  phi's ghosts must be filled.
 template <class R>
 void rbgs(const Field<R>& phi, const Field<R>& rhs, int color) {
   const Level& L = *phi.L;
   const R h2 = (R)(L.h * L.h);
+  const R inv6 = R(1) / R(6);
 #pragma omp parallel for schedule(dynamic)
   for (long long b = 0; b < (long long)L.boxes.size(); ++b) {
     const Box& B = L.boxes[b];
@@ -202,12 +206,13 @@ void rbgs(const Field<R>& phi, const Field<R>& rhs, int color) {
         for (int x = B.lo[0]; x <= B.hi[0]; ++x) {
           if (pmod(x + y + z, 2) != color) continue;
           R s = nbr_sum(phi, (int)b, x, y, z);
-          phi.at((int)b, x, y, z) = (s - h2 * rhs.at((int)b, x, y, z)) / (R)6;
+          phi.at((int)b, x, y, z) = std::fma(-h2, rhs.at((int)b, x, y, z), s) * inv6;
         }
   }
 }
 
-// Residual r = rhs - (s - 6 phi) * (1/h^2) on valid cells (r may be null); returns
+// Residual r = rhs - (s - 6 phi) / h^2, evaluated as fma(-1/h^2, fma(-6, phi, s), rhs), on
+// valid cells (r may be null); returns
 // max |r| (NaN if any residual is NaN).  phi's ghosts must be filled.
 template <class R>
 double residual(const Field<R>& phi, const Field<R>& rhs, const Field<R>* r) {
@@ -222,7 +227,7 @@ double residual(const Field<R>& phi, const Field<R>& rhs, const Field<R>* r) {
       for (int y = B.lo[1]; y <= B.hi[1]; ++y)
         for (int x = B.lo[0]; x <= B.hi[0]; ++x) {
           R s = nbr_sum(phi, (int)b, x, y, z);
-          R v = rhs.at((int)b, x, y, z) - (s - (R)6 * phi.at((int)b, x, y, z)) * ih2;
+          R v = std::fma(-ih2, std::fma((R)-6, phi.at((int)b, x, y, z), s), rhs.at((int)b, x, y, z));
           if (r) r->at((int)b, x, y, z) = v;
           double a = std::fabs((double)v);
           if (std::isnan(a)) nan = true;
@@ -747,14 +752,17 @@ int orc_solve(const int dlo[3], const int dhi[3], const int periodic[3], int nbo
     if (!mixed) {
       vcycle(D, Mb, 0, nu1, nu2);
     } else {
-      // Inner FP32 V-cycle on the residual scaled by its max-norm, FP64 correction add.
+      // Inner FP32 V-cycle on the residual scaled by 2^-e, 2^e <= ||r|| < 2^(e+1) (exact),
+      // FP64 correction add.
+      const double up = std::ldexp(1.0, std::ilogb(rn));
+      const double down = std::ldexp(1.0, -std::ilogb(rn));
       const Level& L = levels[0];
       for (size_t b = 0; b < L.boxes.size(); ++b) {
         const Box& B = L.boxes[b];
         for (int z = B.lo[2]; z <= B.hi[2]; ++z)
           for (int y = B.lo[1]; y <= B.hi[1]; ++y)
             for (int x = B.lo[0]; x <= B.hi[0]; ++x)
-              Df[0].frhs.at((int)b, x, y, z) = (float)(D[0].fr.at((int)b, x, y, z) / rn);
+              Df[0].frhs.at((int)b, x, y, z) = (float)(D[0].fr.at((int)b, x, y, z) * down);
       }
       zero_valid(Df[0].fphi);
       vcycle(Df, Mb, 0, nu1, nu2);
@@ -764,7 +772,7 @@ int orc_solve(const int dlo[3], const int dhi[3], const int periodic[3], int nbo
           for (int y = B.lo[1]; y <= B.hi[1]; ++y)
             for (int x = B.lo[0]; x <= B.hi[0]; ++x)
               D[0].fphi.at((int)b, x, y, z) =
-                  D[0].fphi.at((int)b, x, y, z) + rn * (double)Df[0].fphi.at((int)b, x, y, z);
+                  std::fma(up, (double)Df[0].fphi.at((int)b, x, y, z), D[0].fphi.at((int)b, x, y, z));
       }
     }
     *vcycles = it + 1;
