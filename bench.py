@@ -222,42 +222,9 @@ def run_ours(args, wl_name):
     vcycles = results[-1].vcycles
     assert all(r.status == 0 and r.rel_resid <= 1e-10 for r in results)
 
-    # ---- dominant kernel: red-black half-sweep on the fine level, timed alone
-    reps = 40
-    ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fr32 = None
-    sm_phi, sm_rhs = fp, fr
-    for color in (0, 1):
-        mg.mg_smooth(ctx, sm_phi, sm_rhs, bc, h, color, stream)
-    stream.synchronize()
-    ev_a.record(stream)
-    for k in range(reps):
-        mg.mg_smooth(ctx, sm_phi, sm_rhs, bc, h, k & 1, stream)
-    ev_b.record(stream)
-    stream.synchronize()
-    t_half = ev_a.elapsed_time(ev_b) / reps / 1e3
-    esize = 8
-    alg_bytes = 2 * esize * cells            # phi read + half rhs + half phi write = 16 B/cell
-    peaks, peak_src = load_peaks()
-    achieved = alg_bytes / t_half / 1e9
-    # residual + max-norm kernel (reads phi and rhs: 16 B/cell)
-    ev_a.record(stream)
-    for _ in range(reps):
-        mg.mg_residual(ctx, fp, fr, 0, h, False, stream)
-    ev_b.record(stream)
-    stream.synchronize()
-    t_res = ev_a.elapsed_time(ev_b) / reps / 1e3
-
-    roof = {"kernel": "k_rbgs_half (one colour, 256^3 fine level)" if wl_name == "dirichlet256"
-            else "k_rbgs_half (one colour, fine level)",
-            "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-            "peak_source": peak_src,
-            "traffic": roofline_traffic("rbgs_half", wl_name),
-            "algorithmic_bytes_per_launch": alg_bytes, "launch_us": round(t_half * 1e6, 2),
-            "residual_norm_kernel": {"achieved": round(2 * esize * cells / t_res / 1e9, 1),
-                                     "frac": round(2 * esize * cells / t_res / 1e9 / peaks["hbm_gbs"], 4),
-                                     "launch_us": round(t_res * 1e6, 2)}}
+    # ---- dominant kernels on the fine level, timed alone on the solve stream
+    kt = kernel_timings(ctx, stream, ba, fp, fr, bc, h, cells, box)
+    roof = roofline(kt, wl_name, prec == mg.MG_PREC_F64, clocks)
 
     # ---- end to end through the C ABI with host buffers
     e2e_steps = max(1, min(args.steps, 5))
@@ -303,6 +270,108 @@ def run_ours(args, wl_name):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+FP64_LANES_PER_SM_CLK = 2      # GB300 FP64 pipe: lane-operations per SM per clock
+N_SM = 152
+FP64_INST_PER_UPDATE = 7       # 5 DADD (neighbour sum) + 1 DFMA + 1 DMUL
+FP64_INST_PER_RESIDUAL = 7     # 5 DADD + 2 DFMA
+
+
+def _time(stream, fn, reps):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn(0)
+    stream.synchronize()
+    a.record(stream)
+    for k in range(reps):
+        fn(k)
+    b.record(stream)
+    stream.synchronize()
+    return a.elapsed_time(b) / reps / 1e3
+
+
+def kernel_timings(ctx, stream, ba, fp, fr, bc, h, cells, box, reps=40):
+    """Average launch durations (s) of the fine-level kernels, each launched back to back
+    on `stream` between two CUDA events: FP64 half-sweep, FP64 residual + norm, FP32 fused
+    sweep (out of place), FP32 half-sweep."""
+    from paper_2403_12179_gb300 import mg
+    out = {}
+    mg.mg_fill_boundary(ctx, fp, bc, stream)
+    out["rbgs_half_f64"] = _time(stream, lambda k: mg.mg_smooth(ctx, fp, fr, bc, h, k & 1, stream), reps)
+    out["residual_f64"] = _time(stream, lambda k: mg.mg_residual(ctx, fp, fr, 0, h, False, stream), reps)
+    out["fill_f64_g2"] = _time(stream, lambda k: mg.mg_fill_boundary(ctx, fp, bc, stream), reps)
+    # FP32 fields of the same layout (the mixed form's inner cycle)
+    a32 = mg.mg_fab_alloc(ctx, ba, 1, 2, mg.MG_F32)
+    b32 = mg.mg_fab_alloc(ctx, ba, 1, 2, mg.MG_F32)
+    r32 = mg.mg_fab_alloc(ctx, ba, 1, 1, mg.MG_F32)
+    mg.mg_fab_set_val(ctx, r32, 1.0, True, stream)
+    mg.mg_fill_boundary(ctx, a32, bc, stream)
+    mg.mg_fill_boundary(ctx, b32, bc, stream)
+    pair = (a32, b32)
+    out["rbgs_fused_f32"] = _time(stream, lambda k: mg.mg_smooth_fused(ctx, pair[k & 1], r32, pair[(k + 1) & 1], bc, h, stream), reps)
+    out["rbgs_half_f32"] = _time(stream, lambda k: mg.mg_smooth(ctx, a32, r32, bc, h, k & 1, stream), reps)
+    for f in (a32, b32, r32):
+        mg.mg_fab_free(ctx, f, stream)
+    stream.synchronize()
+    return out
+
+
+def roofline(kt, wl_name, f64, clocks):
+    peaks, src = load_peaks()
+    cells = WORKLOADS[wl_name]["n"] ** 3
+    sm_mhz = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = FP64_LANES_PER_SM_CLK * N_SM * sm_mhz * 1e6 / 1e9      # G lane-ops/s
+    hbm = peaks["hbm_gbs"]
+    t = kt["rbgs_half_f64"]
+    half_ops = FP64_INST_PER_UPDATE * cells / 2
+    fused_bytes = 24 * cells          # read phi, read rhs, write phi: one full sweep
+    extra = {
+        "rbgs_half_f64": {"launch_us": round(t * 1e6, 2),
+                          "hbm_frac": round(16 * cells / t / 1e9 / hbm, 4),
+                          "fp64_frac": round(half_ops / t / 1e9 / fp64_peak, 4)},
+        "residual_f64": {"launch_us": round(kt["residual_f64"] * 1e6, 2),
+                         "fp64_frac": round(FP64_INST_PER_RESIDUAL * cells / kt["residual_f64"] / 1e9 / fp64_peak, 4),
+                         "hbm_frac": round(16 * cells / kt["residual_f64"] / 1e9 / hbm, 4)},
+        "fill_f64_g2": {"launch_us": round(kt["fill_f64_g2"] * 1e6, 2)},
+        "rbgs_fused_f32": {"launch_us": round(kt["rbgs_fused_f32"] * 1e6, 2),
+                           "hbm_frac": round(12 * cells / kt["rbgs_fused_f32"] / 1e9 / hbm, 4)},
+        "rbgs_half_f32": {"launch_us": round(kt["rbgs_half_f32"] * 1e6, 2),
+                          "hbm_frac": round(8 * cells / kt["rbgs_half_f32"] / 1e9 / hbm, 4)},
+    }
+    if f64:
+        ach = half_ops / t / 1e9
+        return {"kernel": "k_rbgs_half<double> (one colour, fine level)", "bound": "alu",
+                "achieved": round(ach, 1), "peak": round(fp64_peak, 1),
+                "unit": "G FP64 lane-ops/s", "frac": round(ach / fp64_peak, 4),
+                "peak_source": f"derived: {FP64_LANES_PER_SM_CLK} FP64 lanes/clk/SM x {N_SM} SMs x {sm_mhz:.0f} MHz",
+                "algorithmic_ops_per_launch": half_ops,
+                "traffic": roofline_traffic("rbgs_half_f64", wl_name), "kernels": extra}
+    t = kt["rbgs_fused_f32"]
+    ach = 12 * cells / t / 1e9
+    return {"kernel": "k_rbgs_fused<float> (full sweep, fine level)", "bound": "hbm",
+            "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+            "peak_source": src, "algorithmic_bytes_per_launch": 12 * cells,
+            "traffic": roofline_traffic("rbgs_fused_f32", wl_name), "kernels": extra}
+
+
+def run_kernels_only(args, wl_name):
+    """Set up the workload's fine level and run only the kernel timing loops (for ncu)."""
+    import torch
+    from paper_2403_12179_gb300 import mg
+    wl = WORKLOADS[wl_name]
+    n, box = wl["n"], wl["box"]
+    ctx = mg.mg_init(0)
+    stream = torch.cuda.Stream()
+    mg.mg_set_stream(ctx, stream)
+    ba = mg.mg_box_array_create(ctx, (0, 0, 0), (n - 1,) * 3, (box,) * 3)
+    fr = mg.mg_fab_alloc(ctx, ba, 1, 1)
+    fp = mg.mg_fab_alloc(ctx, ba, 1, 2)
+    mg.mg_fab_set_val(ctx, fr, 1.0, True, stream)
+    kt = kernel_timings(ctx, stream, ba, fp, fr, mg.make_bc(wl["periodic"]), 1.0 / n, n ** 3, box,
+                        reps=args.steps)
+    mg.mg_finalize(ctx)
+    print(json.dumps({"kernels_only": wl_name, "launch_s": kt}))
 
 
 def mg_launches():
@@ -399,10 +468,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dirichlet256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="time only the fine-level kernels (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.kernels_only:
+        run_kernels_only(args, args.workload)
+    elif args.impl == "reference":
         run_reference(args, args.workload)
     else:
         run_ours(args, args.workload)

@@ -34,17 +34,22 @@ struct Ar;
 template <>
 struct Ar<double> {
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 };
 template <>
 struct Ar<float> {
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 };
+
+// phi = fma(-h^2, rhs, s) * (1/6); mh2 = -h^2
+template <class T>
+__device__ __forceinline__ T gs_update(T s, T rhs, T mh2) {
+  constexpr T inv6 = T(1) / T(6);
+  return Ar<T>::mul(Ar<T>::fma(mh2, rhs, s), inv6);
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -111,7 +116,7 @@ struct Sweep {
   long long plane, planer;
   int flags;             // bit d: low face of dim d is a Dirichlet domain face; bit 3+d: high
   uint32_t pbytes, rbytes;
-  T h2;
+  T mh2;  // -h^2
   int lox, loy, loz;
 };
 
@@ -147,7 +152,7 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(const DRow* __restrict__ row
   S.planer = R.v[1].plane;
   S.gr = R.v[1].g;
   S.flags = R.pad_;
-  S.h2 = (T)R.h2;
+  S.mh2 = -(T)R.h2;
   S.lox = R.lo[0];
   S.loy = R.lo[1];
   S.loz = R.lo[2];
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(const DRow* __restrict__ row
           a = Ar<T>::add(a, P0[o]);
           a = Ar<T>::add(a, P2[o]);
           T q = Q[(y - S.y0 + 1) * S.pr + x + S.gr];
-          P1[o] = Ar<T>::div(Ar<T>::sub(a, Ar<T>::mul(S.h2, q)), (T)6);
+          P1[o] = gs_update(a, q, S.mh2);
         }
       }
     }
@@ -288,7 +293,7 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(const DRow* __restrict__ row
         a = Ar<T>::add(a, B0[o]);
         a = Ar<T>::add(a, B2[o]);
         T q = QB[(y - S.y0 + 1) * S.pr + x + S.gr];
-        B1[o] = Ar<T>::div(Ar<T>::sub(a, Ar<T>::mul(S.h2, q)), (T)6);
+        B1[o] = gs_update(a, q, S.mh2);
       }
       fence_async_smem();
     }
@@ -328,9 +333,13 @@ static cudaError_t launch_fused_t(const DRow* rows, const int2* units, int nunit
   re = (re + align - 1) / align * align;
   size_t smem = ((size_t)NP * pe + (size_t)NR * re) * sizeof(T) + (NP + NR) * 8;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_rbgs_fused<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
+  static size_t opted_in = 0;  // largest dynamic shared memory size already allowed
+  if (smem > opted_in) {
+    cudaError_t e = cudaFuncSetAttribute(k_rbgs_fused<T, D>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    opted_in = smem;
+  }
   k_rbgs_fused<T, D><<<nunits, 256, smem, s>>>(rows, units, ty, pe, re, err);
   count_launches(1);
   return cudaGetLastError();

@@ -4,8 +4,11 @@
 //
 // All stencil kernels are bounded by HBM bandwidth (about 1 flop per byte), so none of them
 // uses the tensor cores.  Each launch covers every box of its table (Sec. 3.2 kernel fusing).
-// Arithmetic goes through __{d,f}{add,sub,mul,div}_rn so that no multiply is contracted into
-// an FMA: every operation is one IEEE round-to-nearest step in the documented order.
+// Arithmetic goes through __{d,f}{add,mul,fma}_rn intrinsics in a fixed order, each one IEEE
+// round-to-nearest step, so results match the documented formulas bit for bit.  On GB300
+// FP64 instructions are scarce (the FP64 pipe issues far fewer lanes per clock than FP32), so
+// the FP64 forms use fused multiply-adds and a multiplication by the rounded 1/6, and sign
+// flips and absolute values are integer operations on the bit pattern.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -22,17 +25,47 @@ struct Ar;
 template <>
 struct Ar<double> {
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  // sign flip and |.| as integer operations (no FP64 pipe instruction)
+  static __device__ __forceinline__ double neg(double a) {
+    return __longlong_as_double(__double_as_longlong(a) ^ (long long)0x8000000000000000ull);
+  }
+  // monotonic key of |a| (NaN above Inf), comparable across a warp
+  static __device__ __forceinline__ unsigned long long abskey(double a) {
+    return (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
+  }
+  // key -> bit pattern of the double |a|
+  static __device__ __forceinline__ unsigned long long key_to_f64bits(unsigned long long k) { return k; }
 };
 template <>
 struct Ar<float> {
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float neg(float a) {
+    return __int_as_float(__float_as_int(a) ^ (int)0x80000000u);
+  }
+  static __device__ __forceinline__ unsigned long long abskey(float a) {
+    return (unsigned long long)((unsigned)__float_as_int(a) & 0x7FFFFFFFu);
+  }
+  static __device__ __forceinline__ unsigned long long key_to_f64bits(unsigned long long k) {
+    return k ? (unsigned long long)__double_as_longlong((double)__int_as_float((int)k)) : 0ull;
+  }
 };
+
+// Gauss-Seidel update and residual of one cell (s = ordered neighbour sum):
+//   update   phi = fma(-h^2, rhs, s) * (1/6)
+//   residual r   = fma(-1/h^2, fma(-6, phi, s), rhs)
+template <class T>
+__device__ __forceinline__ T gs_update(T s, T rhs, T h2) {
+  constexpr T inv6 = T(1) / T(6);
+  return Ar<T>::mul(Ar<T>::fma(Ar<T>::neg(h2), rhs, s), inv6);
+}
+template <class T>
+__device__ __forceinline__ T residual_of(T s, T phi, T rhs, T ih2) {
+  return Ar<T>::fma(Ar<T>::neg(ih2), Ar<T>::fma(T(-6), phi, s), rhs);
+}
 
 constexpr int kWarps = 8;  // warps per block in the row kernels
 constexpr int kThreads = kWarps * 32;
@@ -115,7 +148,7 @@ __global__ void __launch_bounds__(256) k_copy_tags(const DTag* __restrict__ tags
       T v;
       if (t.sign == 0) v = T(0);
       else if (t.sign > 0) v = src[so + c * t.scs];
-      else v = -src[so + c * t.scs];
+      else v = Ar<T>::neg(src[so + c * t.scs]);
       dst[d + c * t.dcs] = v;
     }
   }
@@ -139,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_half(const DRow* __restrict__
     const int par = (color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1;
     for (int x = par + 2 * lane; x < n0; x += 64) {
       T s = nbr_sum(phi + x, vp.pitch, vp.plane);
-      phi[x] = Ar<T>::div(Ar<T>::sub(s, Ar<T>::mul(h2, rhs[x])), (T)6);
+      phi[x] = gs_update(s, rhs[x], h2);
     }
   });
 }
@@ -181,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const DRow* __restrict__ 
     const DRow& R = rows[b];
     if (R.solve != cur) {
       if (cur >= 0 && norms) {
-        unsigned long long m = warp_max(mx);
+        unsigned long long m = Ar<T>::key_to_f64bits(warp_max(mx));
         if (lane == 0 && m) atomicMax(&norms[cur], m);
       }
       cur = R.solve;
@@ -196,13 +229,13 @@ __global__ void __launch_bounds__(kThreads) k_residual(const DRow* __restrict__ 
     const T ih2 = (T)R.ih2;
     for (int x = lane; x < n0; x += 32) {
       T s = nbr_sum(phi + x, vp.pitch, vp.plane);
-      T v = Ar<T>::sub(rhs[x], Ar<T>::mul(Ar<T>::sub(s, Ar<T>::mul((T)6, phi[x])), ih2));
+      T v = residual_of(s, phi[x], rhs[x], ih2);
       if (r) r[x] = v;
-      unsigned long long bits = (unsigned long long)__double_as_longlong(fabs((double)v));
-      mx = bits > mx ? bits : mx;
+      unsigned long long k = Ar<T>::abskey(v);
+      mx = k > mx ? k : mx;
     }
   });
-  if (norms) flush_block_max(mx, cur, norms);
+  if (norms) flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
 }
 
 // Fused residual + restriction.  Lane l of a warp produces coarse cells X = l, l+32, ... of
@@ -231,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_restrict(const DRow* __re
             const T* p = line<T>(vp, 2 * Y + j, 2 * Z + k) + 2 * X + i;
             const T* q = line<T>(vr, 2 * Y + j, 2 * Z + k) + 2 * X + i;
             T s = nbr_sum(p, vp.pitch, vp.plane);
-            T v = Ar<T>::sub(q[0], Ar<T>::mul(Ar<T>::sub(s, Ar<T>::mul((T)6, p[0])), ih2));
+            T v = residual_of(s, p[0], q[0], ih2);
             acc = (i | j | k) ? Ar<T>::add(acc, v) : v;
           }
       crhs[X] = Ar<T>::mul(acc, (T)0.125);
@@ -354,7 +387,7 @@ __global__ void __launch_bounds__(kThreads) k_maxabs(const DRow* __restrict__ ro
     const DRow& R = rows[b];
     if (R.solve != cur) {
       if (cur >= 0) {
-        unsigned long long m = warp_max(mx);
+        unsigned long long m = Ar<T>::key_to_f64bits(warp_max(mx));
         if (lane == 0 && m) atomicMax(&norms[cur], m);
       }
       cur = R.solve;
@@ -364,16 +397,19 @@ __global__ void __launch_bounds__(kThreads) k_maxabs(const DRow* __restrict__ ro
     const int y = (int)(lr % n1), z = (int)(lr / n1);
     const T* f = line<T>(R.v[0], y, z);
     for (int x = lane; x < n0; x += 32) {
-      unsigned long long bits = (unsigned long long)__double_as_longlong(fabs((double)f[x]));
-      mx = bits > mx ? bits : mx;
+      unsigned long long k = Ar<T>::abskey(f[x]);
+      mx = k > mx ? k : mx;
     }
   });
-  flush_block_max(mx, cur, norms);
+  flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
 }
 
 __device__ __forceinline__ double norm_of(const unsigned long long* norms, int solve) {
   return __longlong_as_double((long long)norms[solve]);
 }
+// 2^e with 2^e <= s < 2^(e+1), and its inverse; both exact powers of two
+__device__ __forceinline__ double pow2_floor(double s) { return ldexp(1.0, ilogb(s)); }
+__device__ __forceinline__ double pow2_floor_inv(double s) { return ldexp(1.0, -ilogb(s)); }
 
 __global__ void __launch_bounds__(kThreads) k_residual_scale_f32(const DRow* __restrict__ rows,
                                                                  int nbox, long long nrows,
@@ -389,11 +425,11 @@ __global__ void __launch_bounds__(kThreads) k_residual_scale_f32(const DRow* __r
     const double* rhs = line<double>(R.v[1], y, z);
     float* r32 = line<float>(R.c[0], y, z);
     const double ih2 = R.ih2;
-    const double sc = norm_of(norms, R.solve);
+    const double down = pow2_floor_inv(norm_of(norms, R.solve));
     for (int x = lane; x < n0; x += 32) {
       double s = nbr_sum(phi + x, vp.pitch, vp.plane);
-      double v = __dsub_rn(rhs[x], __dmul_rn(__dsub_rn(s, __dmul_rn(6.0, phi[x])), ih2));
-      r32[x] = __double2float_rn(__ddiv_rn(v, sc));
+      double v = residual_of(s, phi[x], rhs[x], ih2);
+      r32[x] = __double2float_rn(__dmul_rn(v, down));
     }
   });
 }
@@ -408,8 +444,8 @@ __global__ void __launch_bounds__(kThreads) k_correct_add(const DRow* __restrict
     const int y = (int)(lr % n1), z = (int)(lr / n1);
     double* phi = line<double>(R.v[0], y, z);
     const float* e = line<float>(R.c[0], y, z);
-    const double sc = norm_of(norms, R.solve);
-    for (int x = lane; x < n0; x += 32) phi[x] = __dadd_rn(phi[x], __dmul_rn(sc, (double)e[x]));
+    const double up = pow2_floor(norm_of(norms, R.solve));
+    for (int x = lane; x < n0; x += 32) phi[x] = __fma_rn(up, (double)e[x], phi[x]);
   });
 }
 

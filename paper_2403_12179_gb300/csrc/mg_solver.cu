@@ -224,7 +224,11 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
       D.bao = std::make_shared<BoxArrayObj>();
       D.bao->ba = lev[l];
     }
-    const bool want_fused = p.smoother != MG_SMOOTH_HALF && l + 1 < nl;
+    // FP64 levels default to half-sweeps: on GB300 they are bound by the FP64 pipe, and the
+    // fused sweep's redundant ring updates add FP64 work; FP32 levels are bound by HBM
+    // bandwidth, where the fused sweep halves the traffic.
+    const bool want_fused = l + 1 < nl && (p.smoother == MG_SMOOTH_FUSED ||
+                                           (p.smoother == MG_SMOOTH_AUTO && H->dt == DT_F32));
     if (l == 0 && !H->mixed) {
       D.phi = H->phi0;
       D.rhs = H->rhs0;
