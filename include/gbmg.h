@@ -243,6 +243,28 @@ int mg_prolong_add(mg_ctx_t ctx, mg_fab_t coarse, mg_fab_t fine, void* stream);
 int mg_bottom_solve(mg_ctx_t ctx, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, double h,
                     void* stream);
 
+/* Residual max-norm that allocates nothing (the paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code running under a frozen
+ * memory budget, inside a framework that owns every device allocation, or where an
+ * allocation could stall other streams).  It computes the same value as mg_residual's norm,
+ * max |rhs - A phi| over valid cells, without a context or fab handles: the caller passes
+ * the box array (domain and int[6*nbox] boxes) and the device base addresses of two FP64,
+ * 1-component buffers laid out exactly as mg_fab_layout describes for that box array with
+ * phi_nghost (>= 1) and rhs_nghost ghost layers; phi's ghost cells are used as they are.
+ * h <= 0 means 1 / (domain x extent).  The norm is written to the host double *norm; the
+ * call synchronises `stream`.
+ * Scratch: a file-scope device array of 1024 box-table rows plus an 8-byte accumulator
+ * (229,632 bytes), held by every GPU that loads the library until the process exits; no
+ * cudaMalloc, cudaFree or pool allocation happens in this call.  At most 1024 boxes
+ * (MG_EINVAL beyond).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  Every call shares the array and it keeps the last call's contents (the
+ * accumulator is cleared at the start of each call), so calls that overlap on the GPU --
+ * on different streams, or from different host threads -- race. */
+int mg_residual_norm_noalloc(const int dom_lo[3], const int dom_hi[3], int nbox, const int* lo_hi,
+                             const double* phi, int phi_nghost, const double* rhs, int rhs_nghost,
+                             double h, double* norm, void* stream);
+
 /* ---- solves --------------------------------------------------------------------------- */
 
 /* Synchronous V(nu1,nu2) solve of lap(phi) = rhs (FP64 fabs, 1 component, same box array;

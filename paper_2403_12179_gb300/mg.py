@@ -303,6 +303,20 @@ def mg_bottom_solve(ctx, rhs, phi, bc, h, stream=None):
                               ctypes.c_double(h), _s(stream)))
 
 
+def mg_residual_norm_noalloc(dom_lo, dom_hi, boxes, phi_ptr, phi_nghost, rhs_ptr, rhs_nghost,
+                             h=0.0, stream=None):
+    """Residual max-norm through the entry point that allocates no device memory (for
+    callers that cannot allocate); buffers laid out as mg_fab_layout describes."""
+    flat = [int(v) for b in boxes for v in b]
+    arr = (ctypes.c_int * len(flat))(*flat)
+    nrm = ctypes.c_double(0.0)
+    _ck(lib().mg_residual_norm_noalloc(_c_int3(*dom_lo), _c_int3(*dom_hi), ctypes.c_int(len(boxes)),
+                                       arr, ctypes.c_void_p(phi_ptr), ctypes.c_int(phi_nghost),
+                                       ctypes.c_void_p(rhs_ptr), ctypes.c_int(rhs_nghost),
+                                       ctypes.c_double(h), ctypes.byref(nrm), _s(stream)))
+    return nrm.value
+
+
 # ---- solves ----------------------------------------------------------------------------
 
 def mg_solve(ctx, rhs, phi, bc, tol=1e-10, opt=None):
