@@ -82,9 +82,10 @@ typedef struct {
   int status;        /* MG_OK, MG_NOT_CONVERGED, MG_ENAN, ... */
   int vcycles;       /* V-cycles (outer iterations for MG_PREC_MIXED) performed */
   double rel_resid;  /* ||rhs - A phi||_inf / ||rhs||_inf at exit */
-  double seconds;    /* wall time from start of work to completion */
+  double seconds;    /* t_end - t_start: for served solves the latency submit -> done */
   double t_admit;    /* serving: seconds since context creation at admission (else 0) */
-  double t_start;    /* seconds since context creation when work started */
+  double t_start;    /* seconds since context creation when the call started (served:
+                        when mg_submit queued the request) */
   double t_end;      /* seconds since context creation at completion */
 } mg_result;
 
@@ -110,6 +111,10 @@ int mg_version(void);
 
 /* Stream used by mg_solve / mg_solve_batch (default: a stream the context creates). */
 int mg_set_stream(mg_ctx_t ctx, void* stream);
+
+/* Memory pool of the context (Sec. 3.7 arena): its cap and the bytes currently allocated
+ * from it (fabs, coarse levels, tables, scratch).  Either pointer may be NULL. */
+int mg_pool_info(mg_ctx_t ctx, size_t* cap, size_t* in_use);
 
 /* Instrumentation (no counterpart in the paper): number of kernels this process has
  * enqueued through the library so far, counting each kernel node of a replayed CUDA graph
@@ -284,10 +289,15 @@ int mg_solve_batch(mg_ctx_t ctx, int n, const mg_fab_t* rhs, const mg_fab_t* phi
 
 /* ---- serving (continuous batching; no counterpart in the paper) ---------------------- */
 
-/* Queue a solve for the context's scheduler thread, which admits requests while the
- * pool can hold their coarse levels, interleaves V-cycles of all admitted solves in shared
- * launches and retires each solve when it converges.  rhs / phi must stay allocated until
- * mg_poll reports completion.  Errors: MG_EAGAIN (queue full), MG_EINVAL. */
+/* Queue a solve for the context's scheduler thread (started on the first call), which
+ * admits requests in arrival order while a slot is free and the context pool can hold their
+ * coarse levels, runs the V-cycles of all admitted solves in shared launches (one launch per
+ * stage for the whole mix), retires each solve when it converges and releases its coarse
+ * levels in stream order.  A request that cannot fit even into an empty pool completes with
+ * MG_ENOMEM.  rhs / phi must stay allocated, and untouched by other calls, until mg_poll
+ * reports completion; while requests are in flight the context's stream belongs to the
+ * scheduler (use another context for synchronous solves).  Errors: MG_EAGAIN (queue full),
+ * MG_EINVAL. */
 int mg_submit(mg_ctx_t ctx, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, double tol,
               const mg_options* opt, mg_ticket_t* out);
 

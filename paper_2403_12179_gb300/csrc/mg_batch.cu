@@ -1,0 +1,596 @@
+// Batched and served solves.
+//
+// Many independent solves advance together: each stage of the V-cycle is ONE launch whose row
+// space is the concatenation of the participating solves' cached box tables (segment lists,
+// the multi-solve analogue of the fused launch over all boxes of Sec. 3.2).  A solve's
+// arithmetic does not depend on its company, so each result is bit-identical to the same
+// solve run alone.  Solves converge and retire independently.
+//
+// Serving (mg_submit / mg_poll) runs the same step on a scheduler thread with continuous
+// batching: requests are admitted while the pool can hold their coarse levels and a slot is
+// free, their V-cycles share launches with the solves already running, and each solve's
+// hierarchy is released in stream order when it retires (Sec. 3.7 async-safe arena).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "mg_runtime.hpp"
+#include "mg_solver.hpp"
+
+namespace gbmg {
+
+namespace {
+
+double bits2d(unsigned long long b) {
+  double d;
+  std::memcpy(&d, &b, 8);
+  return d;
+}
+
+// One solve inside a batched step.
+struct Member {
+  std::shared_ptr<Hierarchy> H;
+  int slot = 0;            // norms[slot]: residual norm, norms[slot + 1]: rhs norm
+  double tol = 1e-10;
+  double rhsnorm = 0, rn = 0;
+  int vcycles = 0;
+  int status = MG_OK;
+  bool started = false;    // first norm check taken
+  bool done = false;
+  bool zero_rhs = false;
+  mg_result res{};
+  int64_t ticket = 0;
+  double t_submit = -1.0;  // served solves: submission time
+};
+
+// Segment-list builders (host side); offsets into the step's packed upload.
+struct SegB {
+  std::vector<Seg> v;
+  long long total = 0;
+  size_t off = 0;
+  void add(const OpTable& t, int slot) {
+    if (!t.nrows) return;
+    Seg s{};
+    s.rows = t.rows();
+    s.row_begin = total;
+    s.nbox = t.nbox;
+    s.slot = slot;
+    v.push_back(s);
+    total += t.nrows;
+  }
+};
+struct TagB {
+  std::vector<TagSeg> v;
+  long long total = 0;
+  size_t off = 0;
+  void add(const FillPlan& P, void* base) {
+    if (!P.nchunks) return;
+    TagSeg s{};
+    s.tags = (const DTag*)P.tags->p;
+    s.chunks = (const int2*)P.chunks->p;
+    s.base = base;
+    s.chunk_begin = total;
+    s.nchunks = P.nchunks;
+    v.push_back(s);
+    total += P.nchunks;
+  }
+};
+struct UnitB {
+  std::vector<UnitSeg> v;
+  long long total = 0;
+  size_t off = 0;
+  int ty = 1, depth = 2, mp = 0, mpr = 0;
+  void add(const FusedTable& t) {
+    UnitSeg s{};
+    s.rows = t.rows.rows();
+    s.units = (const int2*)t.units->p;
+    s.unit_begin = total;
+    s.nunits = t.nunits;
+    v.push_back(s);
+    total += t.nunits;
+    ty = std::max(ty, t.ty);
+    depth = std::min(depth, t.depth);
+    mp = std::max(mp, t.max_pitch);
+    mpr = std::max(mpr, t.max_pitch_r);
+  }
+};
+struct JobB {
+  std::vector<BottomJob> v;
+  int maxN = 0;
+  size_t off = 0;
+  void add(const Hierarchy& H) {
+    v.push_back(H.job_host);
+    maxN = std::max(maxN, H.N);
+  }
+};
+
+struct LevelLists {
+  SegB half, half_all, rr, prolong;
+  TagB fill1_half, fill1_all, fill2_phi, fill2_phi2, fill_rhs;
+  UnitB fab, fba;
+  JobB bottom_next;  // bottoms at level l + 1
+};
+
+struct StepLists {
+  std::vector<LevelLists> L;
+  JobB bottom0;
+  SegB resid0, rhsabs0, scale0, correct0, zero0;
+  TagB fill_phi0;
+  int dt = DT_F64;
+  bool mixed = false;
+  int nu1 = 2, nu2 = 2;
+};
+
+struct Staging {
+  std::vector<unsigned char> host;
+  DevBufP dev;
+  template <class T>
+  size_t push(const std::vector<T>& v) {
+    size_t off = (host.size() + 15) / 16 * 16;
+    host.resize(off + v.size() * sizeof(T));
+    if (!v.empty()) std::memcpy(host.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
+
+SegList mk(const SegB& b, const unsigned char* dev) {
+  SegList L{};
+  L.n = (int)b.v.size();
+  if (L.n == 1) L.one = b.v[0];
+  else L.segs = (const Seg*)(dev + b.off);
+  return L;
+}
+TagList mk(const TagB& b, const unsigned char* dev) {
+  TagList L{};
+  L.n = (int)b.v.size();
+  if (L.n == 1) L.one = b.v[0];
+  else L.segs = (const TagSeg*)(dev + b.off);
+  return L;
+}
+UnitList mk(const UnitB& b, const unsigned char* dev) {
+  UnitList L{};
+  L.n = (int)b.v.size();
+  if (L.n == 1) L.one = b.v[0];
+  else L.segs = (const UnitSeg*)(dev + b.off);
+  return L;
+}
+
+// Lists for one step.  `run`: members doing a V-cycle this step; `check`: members whose norm
+// is taken at the end of the step (run plus newly admitted ones); `fresh`: members whose
+// rhs norm is still unknown.
+void build_lists(Ctx& c, StepLists& S, const std::vector<Member*>& run,
+                 const std::vector<Member*>& check, const std::vector<Member*>& fresh) {
+  size_t Lmax = 0;
+  for (Member* m : run) Lmax = std::max(Lmax, m->H->L.size());
+  S.L.assign(Lmax > 0 ? Lmax : 1, LevelLists{});
+  for (Member* m : run) {
+    Hierarchy& H = *m->H;
+    S.dt = H.dt;
+    S.mixed = H.mixed;
+    S.nu1 = H.p.nu1;
+    S.nu2 = H.p.nu2;
+    const int nl = (int)H.L.size();
+    if (nl == 1) S.bottom0.add(H);
+    for (int l = 0; l + 1 < nl; ++l) {
+      LevelData& D = H.L[l];
+      LevelLists& LL = S.L[l];
+      if (D.fused) {
+        LL.fab.add(D.f_ab);
+        LL.fba.add(D.f_ba);
+        LL.fill2_phi.add(fill_plan(c, *D.phi, &H.bc), D.phi->base);
+        LL.fill2_phi2.add(fill_plan(c, *D.phi2, &H.bc), D.phi2->base);
+        LL.fill_rhs.add(fill_plan(c, *D.rhs, &H.bc), D.rhs->base);
+      } else {
+        LL.half.add(D.smooth, m->slot);
+        LL.fill1_half.add(fill_plan(c, *D.phi, &H.bc, 1), D.phi->base);
+      }
+      LL.fill1_all.add(fill_plan(c, *D.phi, &H.bc, 1), D.phi->base);
+      LL.half_all.add(D.smooth, m->slot);
+      LL.rr.add(D.rr, m->slot);
+      LL.prolong.add(D.prolong, m->slot);
+      if (l + 2 == nl) LL.bottom_next.add(H);
+    }
+    if (H.mixed) {
+      S.scale0.add(H.scale0, m->slot);
+      S.correct0.add(H.correct0, m->slot);
+      S.zero0.add(H.L[0].zero, m->slot);
+    }
+  }
+  for (Member* m : check) {
+    S.resid0.add(m->H->resid0, m->slot);
+    S.fill_phi0.add(fill_plan(c, *m->H->phi0, &m->H->bc, 1), m->H->phi0->base);
+  }
+  for (Member* m : fresh) S.rhsabs0.add(m->H->rhsabs0, m->slot);
+}
+
+void upload_lists(Ctx& c, StepLists& S, Staging& st, cudaStream_t s) {
+  st.host.clear();
+  auto seg = [&](SegB& b) { b.off = st.push(b.v); };
+  auto tag = [&](TagB& b) { b.off = st.push(b.v); };
+  auto unit = [&](UnitB& b) { b.off = st.push(b.v); };
+  auto job = [&](JobB& b) { b.off = st.push(b.v); };
+  for (LevelLists& LL : S.L) {
+    seg(LL.half); seg(LL.half_all); seg(LL.rr); seg(LL.prolong);
+    tag(LL.fill1_half); tag(LL.fill1_all); tag(LL.fill2_phi); tag(LL.fill2_phi2); tag(LL.fill_rhs);
+    unit(LL.fab); unit(LL.fba);
+    job(LL.bottom_next);
+  }
+  job(S.bottom0);
+  seg(S.resid0); seg(S.rhsabs0); seg(S.scale0); seg(S.correct0); seg(S.zero0);
+  tag(S.fill_phi0);
+  size_t need = std::max<size_t>(st.host.size(), 256);
+  if (!st.dev || st.dev->bytes < need) {
+    MG_CK(cudaStreamSynchronize(s));
+    if (st.dev) st.dev->reset(s);
+    st.dev = c.alloc(need * 2, s);
+  }
+  MG_CK(cudaMemcpyAsync(st.dev->p, st.host.data(), st.host.size(), cudaMemcpyHostToDevice, s));
+}
+
+void fill_l(Ctx& c, int dt, const TagB& b, const unsigned char* dev, cudaStream_t s) {
+  (void)c;
+  if (b.total) MG_CK(launch_copy_tags_l(dt, mk(b, dev), b.total, 1, s));
+}
+
+void smooth_l(Ctx& c, StepLists& S, LevelLists& LL, int sweeps, const unsigned char* dev,
+              int* err, cudaStream_t s) {
+  int k = 0;
+  for (; k + 1 < sweeps; k += 2) {
+    if (LL.fab.total) {
+      fill_l(c, S.dt, LL.fill2_phi, dev, s);
+      MG_CK(launch_rbgs_fused_l(S.dt, mk(LL.fab, dev), LL.fab.total, LL.fab.ty, LL.fab.depth,
+                                LL.fab.mp, LL.fab.mpr, err, s));
+      fill_l(c, S.dt, LL.fill2_phi2, dev, s);
+      MG_CK(launch_rbgs_fused_l(S.dt, mk(LL.fba, dev), LL.fba.total, LL.fba.ty, LL.fba.depth,
+                                LL.fba.mp, LL.fba.mpr, err, s));
+    }
+    if (LL.half.total)
+      for (int j = 0; j < 2; ++j)
+        for (int color = 0; color < 2; ++color) {
+          fill_l(c, S.dt, LL.fill1_half, dev, s);
+          MG_CK(launch_rbgs_half_l(S.dt, mk(LL.half, dev), LL.half.total, color, s));
+        }
+  }
+  for (; k < sweeps; ++k)
+    for (int color = 0; color < 2; ++color) {
+      // an odd sweep: every member with half-sweeps (fused members too, in place)
+      fill_l(c, S.dt, LL.fill1_all, dev, s);
+      MG_CK(launch_rbgs_half_l(S.dt, mk(LL.half_all, dev), LL.half_all.total, color, s));
+    }
+}
+
+// The step: V-cycle for the `run` members, then the norm check of the `check` members.
+void enqueue_step(Ctx& c, StepLists& S, const unsigned char* dev, unsigned long long* norms,
+                  size_t norm_bytes, bool any_fresh, cudaStream_t s) {
+  int* err = (int*)c.d_err->p;
+  const int nlev = (int)S.L.size();
+  if (S.mixed && S.scale0.total) {
+    MG_CK(launch_residual_scale_f32_l(mk(S.scale0, dev), S.scale0.total, norms, s));
+    MG_CK(launch_set_valid_l(DT_F32, mk(S.zero0, dev), S.zero0.total, 0.0, s));
+  }
+  if (!S.bottom0.v.empty())
+    MG_CK(launch_bottom(S.dt, (const BottomJob*)(dev + S.bottom0.off), (int)S.bottom0.v.size(),
+                        S.bottom0.maxN, s));
+  for (int l = 0; l < nlev; ++l) {
+    LevelLists& LL = S.L[l];
+    if (!LL.rr.total) continue;
+    if (LL.fill_rhs.total) fill_l(c, S.dt, LL.fill_rhs, dev, s);
+    smooth_l(c, S, LL, S.nu1, dev, err, s);
+    fill_l(c, S.dt, LL.fill1_all, dev, s);
+    MG_CK(launch_residual_restrict_l(S.dt, mk(LL.rr, dev), LL.rr.total, s));
+    if (!LL.bottom_next.v.empty())
+      MG_CK(launch_bottom(S.dt, (const BottomJob*)(dev + LL.bottom_next.off),
+                          (int)LL.bottom_next.v.size(), LL.bottom_next.maxN, s));
+  }
+  for (int l = nlev - 1; l >= 0; --l) {
+    LevelLists& LL = S.L[l];
+    if (!LL.prolong.total) continue;
+    MG_CK(launch_prolong_add_l(S.dt, mk(LL.prolong, dev), LL.prolong.total, s));
+    smooth_l(c, S, LL, S.nu2, dev, err, s);
+  }
+  if (S.mixed && S.correct0.total)
+    MG_CK(launch_correct_add_l(mk(S.correct0, dev), S.correct0.total, norms, s));
+  // norm check
+  MG_CK(cudaMemsetAsync(norms, 0, norm_bytes, s));
+  if (any_fresh && S.rhsabs0.total)
+    MG_CK(launch_maxabs_l(DT_F64, mk(S.rhsabs0, dev), S.rhsabs0.total, norms, s));
+  fill_l(c, DT_F64, S.fill_phi0, dev, s);
+  if (S.resid0.total) MG_CK(launch_residual_l(DT_F64, mk(S.resid0, dev), S.resid0.total, norms, s));
+}
+
+// Applies the stop rule of a single solve to a member after its norm check.
+void decide(Ctx& c, Member& m, cudaStream_t s) {
+  const SolveParams& p = m.H->p;
+  if (std::isnan(m.rhsnorm) || std::isinf(m.rhsnorm)) { m.status = MG_ENAN; m.done = true; return; }
+  if (m.rhsnorm == 0.0) {
+    const OpTable& z = m.H->zero0_64;
+    MG_CK(launch_set_valid(DT_F64, z.rows(), z.nbox, z.nrows, 0.0, s));
+    m.rn = 0.0;
+    m.done = true;
+    return;
+  }
+  if (std::isnan(m.rn) || std::isinf(m.rn)) { m.status = MG_ENAN; m.done = true; return; }
+  if (p.fixed_vcycles >= 0) {
+    if (m.vcycles == p.fixed_vcycles) m.done = true;
+    return;
+  }
+  if (m.rn <= m.tol * m.rhsnorm) { m.done = true; return; }
+  if (m.vcycles == p.max_iter) { m.status = MG_NOT_CONVERGED; m.done = true; }
+  (void)c;
+}
+
+void finish(Ctx& c, Member& m) {
+  m.res.status = m.status;
+  m.res.vcycles = m.vcycles;
+  m.res.rel_resid = m.rhsnorm > 0 ? m.rn / m.rhsnorm : 0.0;
+  m.res.t_end = c.now();
+  m.res.seconds = m.res.t_end - m.res.t_start;
+}
+
+// Runs one step for `run` (V-cycle) and `check` (norm check) members of one precision, reads
+// the norms back and applies the stop rule.
+void step_and_decide(Ctx& c, Staging& st, std::vector<Member*>& run, std::vector<Member*>& check,
+                     int nslots, cudaStream_t s) {
+  std::vector<Member*> fresh;
+  for (Member* m : check)
+    if (!m->started) fresh.push_back(m);
+  StepLists S;
+  build_lists(c, S, run, check, fresh);
+  if (!check.empty()) {
+    S.dt = check[0]->H->dt;
+    S.mixed = check[0]->H->mixed;
+  }
+  upload_lists(c, S, st, s);
+  unsigned long long* norms = (unsigned long long*)c.d_norms->p;
+  const size_t nbytes = (size_t)nslots * 8;
+  enqueue_step(c, S, (const unsigned char*)st.dev->p, norms, nbytes, !fresh.empty(), s);
+  MG_CK(cudaMemcpyAsync(c.h_norms, norms, nbytes, cudaMemcpyDeviceToHost, s));
+  MG_CK(cudaStreamSynchronize(s));
+  check_device_error(c);
+  for (Member* m : run) m->vcycles += 1;
+  for (Member* m : check) {
+    if (!m->started) {
+      m->rhsnorm = bits2d(c.h_norms[m->slot + 1]);
+      m->started = true;
+    }
+    m->rn = bits2d(c.h_norms[m->slot]);
+    decide(c, *m, s);
+  }
+  MG_CK(cudaStreamSynchronize(s));  // a zero-rhs member's phi reset completes before it retires
+}
+
+}  // namespace
+
+int solve_batch(Ctx& c, int n, const int64_t* rhs, const int64_t* phi, const mg_bc* bcs, double tol,
+                const SolveParams& p, mg_result* res) {
+  c.require_device();
+  if (!(tol >= 0)) fail(MG_EINVAL, "tol must be >= 0");
+  cudaStream_t s = c.stream;
+  std::vector<Member> M(n);
+  const double t0 = c.now();
+  for (int i = 0; i < n; ++i) {
+    auto fr = c.get_fab(rhs[i]);
+    auto fp = c.get_fab(phi[i]);
+    for (int j = 0; j < i; ++j)
+      if (phi[j] == phi[i]) fail(MG_EINVAL, "a phi fab appears twice in the batch");
+    SolveParams pi = p;  // the default cell size belongs to each solve's own domain
+    if (!(pi.h > 0)) pi.h = 1.0 / fp->ba->ba.dom.len(0);
+    std::lock_guard<std::recursive_mutex> hl(c.hier_mu);
+    Hierarchy& H = get_hierarchy(c, *fr, *fp, &bcs[i], pi);
+    for (auto& h : c.hier)
+      if (h.get() == &H) M[i].H = h;
+    if (!M[i].H) fail(MG_EINVAL, "internal: hierarchy not found");
+    M[i].slot = 2 * i;
+    M[i].tol = tol;
+    M[i].res.t_start = t0;
+  }
+  c.ensure_norm_slots(2 * n);
+  Staging st;
+  std::vector<Member*> run, check;
+  for (auto& m : M) check.push_back(&m);
+  step_and_decide(c, st, run, check, 2 * n, s);
+  for (;;) {
+    run.clear();
+    for (auto& m : M)
+      if (!m.done) run.push_back(&m);
+    if (run.empty()) break;
+    check = run;
+    step_and_decide(c, st, run, check, 2 * n, s);
+  }
+  int rc = MG_OK;
+  for (int i = 0; i < n; ++i) {
+    finish(c, M[i]);
+    if (res) res[i] = M[i].res;
+    if (M[i].status != MG_OK && rc == MG_OK) rc = M[i].status;
+  }
+  if (st.dev) st.dev->reset(s);
+  MG_CK(cudaStreamSynchronize(s));
+  return rc;
+}
+
+// ---- serving ---------------------------------------------------------------------------
+
+struct Ctx::Server {
+  struct Req {
+    int64_t ticket, rhs, phi;
+    mg_bc bc;
+    double tol;
+    SolveParams p;
+    double t_submit;
+  };
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Req> queue;
+  std::map<int64_t, mg_result> done;
+  std::map<int64_t, bool> known;
+  int64_t next_ticket = 1;
+  bool stop = false;
+  std::thread th;
+  size_t max_queue = 1 << 20;
+  int max_active = 4096;
+};
+
+namespace {
+
+void server_loop(Ctx* c) {
+  Ctx::Server& S = *c->server;
+  cudaSetDevice(c->device);
+  cudaStream_t s = c->stream;
+  Staging st;
+  std::vector<std::unique_ptr<Member>> active;
+  std::vector<int> free_slots;
+  int nslots = 0;
+  for (;;) {
+    std::vector<Ctx::Server::Req> admit;
+    {
+      std::unique_lock<std::mutex> lk(S.mu);
+      if (active.empty())
+        S.cv_work.wait(lk, [&] { return S.stop || !S.queue.empty(); });
+      if (S.stop && S.queue.empty() && active.empty()) break;
+      // admission: while a slot is free (pool room is checked when the hierarchy is built)
+      while (!S.queue.empty() && (int)(active.size() + admit.size()) < S.max_active) {
+        admit.push_back(S.queue.front());
+        S.queue.pop_front();
+      }
+    }
+    std::vector<Member*> fresh_members;
+    for (size_t k = 0; k < admit.size(); ++k) {
+      const auto& r = admit[k];
+      std::unique_ptr<Member> m(new Member);
+      m->ticket = r.ticket;
+      m->tol = r.tol;
+      m->t_submit = r.t_submit;
+      m->res.t_admit = c->now();
+      m->res.t_start = r.t_submit;
+      try {
+        auto fr = c->get_fab(r.rhs);
+        auto fp = c->get_fab(r.phi);
+        std::lock_guard<std::recursive_mutex> hl(c->hier_mu);
+        Hierarchy& H = get_hierarchy(*c, *fr, *fp, &r.bc, r.p);
+        for (auto& h : c->hier)
+          if (h.get() == &H) m->H = h;
+      } catch (const MgError& e) {
+        if (e.code == MG_ENOMEM && !active.empty()) {
+          // no room: back to the head of the queue until a running solve retires
+          std::lock_guard<std::mutex> lk(S.mu);
+          for (size_t j = admit.size(); j-- > k;) S.queue.push_front(admit[j]);
+          break;
+        }
+        m->status = e.code;
+        m->done = true;
+        finish(*c, *m);
+        std::lock_guard<std::mutex> lk(S.mu);
+        S.done[m->ticket] = m->res;
+        S.cv_done.notify_all();
+        continue;
+      }
+      if (free_slots.empty()) {
+        free_slots.push_back(nslots);
+        nslots += 2;
+      }
+      m->slot = free_slots.back();
+      free_slots.pop_back();
+      fresh_members.push_back(m.get());
+      active.push_back(std::move(m));
+    }
+    try {
+      c->ensure_norm_slots(nslots);
+      // one step per precision group: running members cycle, every member's norm is checked
+      for (int dt : {DT_F64, DT_F32}) {
+        std::vector<Member*> run, check;
+        for (auto& m : active) {
+          if (m->done || m->H->dt != dt) continue;
+          check.push_back(m.get());
+          if (m->started) run.push_back(m.get());
+        }
+        if (!check.empty()) step_and_decide(*c, st, run, check, nslots, s);
+      }
+    } catch (const MgError& e) {
+      for (auto& m : active) {
+        m->status = e.code;
+        m->done = true;
+      }
+    }
+    // retire
+    std::vector<std::unique_ptr<Member>> keep;
+    for (auto& m : active) {
+      if (!m->done) {
+        keep.push_back(std::move(m));
+        continue;
+      }
+      finish(*c, *m);
+      free_slots.push_back(m->slot);
+      const int64_t rid = m->H ? m->H->rhs_id : 0, pid = m->H ? m->H->phi_id : 0;
+      m->H.reset();
+      // release the solve's hierarchy (coarse levels, tables) in stream order
+      {
+        std::lock_guard<std::recursive_mutex> hl(c->hier_mu);
+        std::vector<std::shared_ptr<Hierarchy>> rest;
+        for (auto& h : c->hier)
+          if (!(h->rhs_id == rid && h->phi_id == pid)) rest.push_back(h);
+        c->hier.swap(rest);
+      }
+      std::lock_guard<std::mutex> lk(S.mu);
+      S.done[m->ticket] = m->res;
+      S.cv_done.notify_all();
+    }
+    active.swap(keep);
+  }
+  if (st.dev) st.dev->reset(s);
+  cudaStreamSynchronize(s);
+}
+
+}  // namespace
+
+int server_submit(Ctx& c, int64_t rhs, int64_t phi, const mg_bc* bc, double tol,
+                  const SolveParams& p, int64_t* ticket) {
+  c.require_device();
+  if (!(tol >= 0)) fail(MG_EINVAL, "tol must be >= 0");
+  int per[3];
+  bc_code(bc, per);
+  c.get_fab(rhs);
+  c.get_fab(phi);
+  if (!c.server) {
+    c.server = std::make_shared<Ctx::Server>();
+    c.server->th = std::thread(server_loop, &c);
+  }
+  Ctx::Server& S = *c.server;
+  std::lock_guard<std::mutex> lk(S.mu);
+  if (S.queue.size() >= S.max_queue) fail(MG_EAGAIN, "serving queue full");
+  Ctx::Server::Req r{S.next_ticket++, rhs, phi, *bc, tol, p, c.now()};
+  S.known[r.ticket] = true;
+  S.queue.push_back(r);
+  *ticket = r.ticket;
+  S.cv_work.notify_one();
+  return MG_OK;
+}
+
+int server_poll(Ctx& c, int64_t ticket, int timeout_ms, mg_result* res) {
+  if (!c.server) fail(MG_EINVAL, "unknown ticket");
+  Ctx::Server& S = *c.server;
+  std::unique_lock<std::mutex> lk(S.mu);
+  if (!S.known.count(ticket)) fail(MG_EINVAL, "unknown ticket");
+  auto ready = [&] { return S.done.count(ticket) > 0; };
+  if (timeout_ms < 0) S.cv_done.wait(lk, ready);
+  else if (timeout_ms > 0) S.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+  if (!ready()) return MG_PENDING;
+  if (res) *res = S.done[ticket];
+  S.done.erase(ticket);
+  S.known.erase(ticket);
+  return MG_OK;
+}
+
+void server_stop(Ctx& c) {
+  if (!c.server) return;
+  {
+    std::lock_guard<std::mutex> lk(c.server->mu);
+    c.server->stop = true;
+    c.server->cv_work.notify_all();
+  }
+  if (c.server->th.joinable()) c.server->th.join();
+  c.server.reset();
+}
+
+}  // namespace gbmg

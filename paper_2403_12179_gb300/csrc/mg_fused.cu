@@ -123,11 +123,18 @@ struct Sweep {
 }  // namespace
 
 // Shared memory: NP phi buffers, NR rhs buffers, then NP + NR mbarriers.
+__device__ __forceinline__ int find_unitseg(const UnitSeg* __restrict__ segs, int n, long long u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_rbgs_fused(const DRow* __restrict__ rows,
-                                                    const int2* __restrict__ units, int ty_max,
-                                                    unsigned phi_buf_elems, unsigned rhs_buf_elems,
-                                                    int* __restrict__ err) {
+__global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsigned phi_buf_elems,
+                                                    unsigned rhs_buf_elems, int* __restrict__ err) {
   constexpr int NP = 4 + D;  // live phi planes s-2..s+1 plus D in flight
   constexpr int NR = 2 + D;  // live rhs planes s-1, s plus D in flight
   extern __shared__ __align__(128) unsigned char smem[];
@@ -137,8 +144,10 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(const DRow* __restrict__ row
   uint64_t* pbar = bars;
   uint64_t* rbar = bars + NP;
 
-  const int2 u = units[blockIdx.x];
-  const DRow& R = rows[u.x];
+  UnitSeg U = L.one;
+  if (L.n > 1) U = L.segs[find_unitseg(L.segs, L.n, blockIdx.x)];
+  const int2 u = U.units[blockIdx.x - U.unit_begin];
+  const DRow& R = U.rows[u.x];
   Sweep<T> S;
   S.nx = R.n[0];
   S.ny = R.n[1];
@@ -323,8 +332,8 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(const DRow* __restrict__ row
 }
 
 template <class T, int D>
-static cudaError_t launch_fused_t(const DRow* rows, const int2* units, int nunits, int ty,
-                                  int max_pitch, int max_pitch_r, int* err, cudaStream_t s) {
+static cudaError_t launch_fused_t(const UnitList& L, long long nunits, int ty, int max_pitch,
+                                  int max_pitch_r, int* err, cudaStream_t s) {
   constexpr int NP = 4 + D, NR = 2 + D;
   unsigned pe = (unsigned)((ty + 4) * max_pitch);
   unsigned re = (unsigned)((ty + 2) * max_pitch_r);
@@ -340,7 +349,7 @@ static cudaError_t launch_fused_t(const DRow* rows, const int2* units, int nunit
     if (e != cudaSuccess) return e;
     opted_in = smem;
   }
-  k_rbgs_fused<T, D><<<nunits, 256, smem, s>>>(rows, units, ty, pe, re, err);
+  k_rbgs_fused<T, D><<<(unsigned)nunits, 256, smem, s>>>(L, ty, pe, re, err);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -354,16 +363,27 @@ size_t fused_smem_bytes(int dt, int ty, int max_pitch, int max_pitch_r, int dept
   return (NP * pe + NR * re) * es + (NP + NR) * 8;
 }
 
+cudaError_t launch_rbgs_fused_l(int dt, const UnitList& L, long long nunits, int ty, int depth,
+                                int max_pitch, int max_pitch_r, int* err, cudaStream_t s) {
+  if (nunits <= 0) return cudaSuccess;
+  if (dt == DT_F64) {
+    if (depth <= 1) return launch_fused_t<double, 1>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+    return launch_fused_t<double, 2>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+  }
+  if (depth <= 1) return launch_fused_t<float, 1>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+  return launch_fused_t<float, 2>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+}
+
 cudaError_t launch_rbgs_fused(int dt, const DRow* rows, const int2* units, int nunits, int ty,
                               int depth, int max_pitch, int max_pitch_r, int* err,
                               cudaStream_t s) {
-  if (nunits <= 0) return cudaSuccess;
-  if (dt == DT_F64) {
-    if (depth <= 1) return launch_fused_t<double, 1>(rows, units, nunits, ty, max_pitch, max_pitch_r, err, s);
-    return launch_fused_t<double, 2>(rows, units, nunits, ty, max_pitch, max_pitch_r, err, s);
-  }
-  if (depth <= 1) return launch_fused_t<float, 1>(rows, units, nunits, ty, max_pitch, max_pitch_r, err, s);
-  return launch_fused_t<float, 2>(rows, units, nunits, ty, max_pitch, max_pitch_r, err, s);
+  UnitList L{};
+  L.one.rows = rows;
+  L.one.units = units;
+  L.one.unit_begin = 0;
+  L.one.nunits = nunits;
+  L.n = 1;
+  return launch_rbgs_fused_l(dt, L, nunits, ty, depth, max_pitch, max_pitch_r, err, s);
 }
 
 }  // namespace gbmg

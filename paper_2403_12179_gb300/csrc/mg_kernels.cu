@@ -79,19 +79,46 @@ __device__ __forceinline__ int find_box(const DRow* __restrict__ rows, int nbox,
   return lo;
 }
 
-// Block k owns rows [k*per, (k+1)*per); warp w of the block takes rows begin+w, +kWarps, ...
-// f(box, row-within-box) is called once per row with all 32 lanes active.
+__device__ __forceinline__ int find_seg(const Seg* __restrict__ segs, int n, long long r) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].row_begin <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Block k owns launch rows [k*per, (k+1)*per); warp w of the block takes rows begin+w,
+// +kWarps, ...  f(row, row-within-box, slot) is called once per row with all 32 lanes active.
 template <class F>
-__device__ __forceinline__ void for_rows(const DRow* __restrict__ rows, int nbox, long long nrows,
-                                         long long per, F&& f) {
+__device__ __forceinline__ void for_rows(const SegList& L, long long nrows, long long per, F&& f) {
   long long begin = (long long)blockIdx.x * per;
   long long end = begin + per < nrows ? begin + per : nrows;
   long long r = begin + (threadIdx.x >> 5);
   if (r >= end) return;
-  int b = find_box(rows, nbox, r);
+  int si = 0;
+  Seg S = L.one;
+  if (L.n > 1) {
+    si = find_seg(L.segs, L.n, r);
+    S = L.segs[si];
+  }
+  int b = find_box(S.rows, S.nbox, r - S.row_begin);
   for (; r < end; r += kWarps) {
-    while (b + 1 < nbox && rows[b + 1].row0 <= r) ++b;
-    f(b, r - rows[b].row0);
+    if (L.n > 1) {
+      bool moved = false;
+      while (si + 1 < L.n && L.segs[si + 1].row_begin <= r) {
+        ++si;
+        moved = true;
+      }
+      if (moved) {
+        S = L.segs[si];
+        b = 0;
+      }
+    }
+    const long long lr = r - S.row_begin;
+    while (b + 1 < S.nbox && S.rows[b + 1].row0 <= lr) ++b;
+    const DRow& R = S.rows[b];
+    f(R, lr - R.row0, S.slot);
   }
 }
 
@@ -122,21 +149,29 @@ __device__ __forceinline__ T* line(const DView& v, int y, int z) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Copy tags (ghost fill, dense scatter / gather).  One warp per chunk of kTagChunk
-// destination cells of one tag; lanes walk the tag region x fastest.
+// Copy tags (ghost fill).  One warp per chunk of kTagChunk destination cells of one tag;
+// lanes walk the tag region x fastest.  Segments = fabs.
+__device__ __forceinline__ int find_tagseg(const TagSeg* __restrict__ segs, int n, long long w) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].chunk_begin <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <class T>
-__global__ void __launch_bounds__(256) k_copy_tags(const DTag* __restrict__ tags,
-                                                   const int2* __restrict__ chunks, int nchunks,
-                                                   void* const* __restrict__ bases, int ncomp) {
-  int w = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+__global__ void __launch_bounds__(256) k_copy_tags(TagList L, long long nchunks, int ncomp) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (w >= nchunks) return;
   const int lane = threadIdx.x & 31;
-  const int2 ch = chunks[w];
-  const DTag t = tags[ch.x];
+  TagSeg S = L.one;
+  if (L.n > 1) S = L.segs[find_tagseg(L.segs, L.n, w)];
+  const int2 ch = S.chunks[w - S.chunk_begin];
+  const DTag t = S.tags[ch.x];
   const int ncell = t.ex * t.ey * t.ez;
   const int end = min(ch.y + kTagChunk, ncell);
-  const T* __restrict__ src = (const T*)bases[t.base_src];
-  T* __restrict__ dst = (T*)bases[t.base_dst];
+  T* __restrict__ base = (T*)S.base;
   for (int l = ch.y + lane; l < end; l += 32) {
     int x = l % t.ex;
     int q = l / t.ex;
@@ -147,9 +182,9 @@ __global__ void __launch_bounds__(256) k_copy_tags(const DTag* __restrict__ tags
     for (int c = 0; c < ncomp; ++c) {
       T v;
       if (t.sign == 0) v = T(0);
-      else if (t.sign > 0) v = src[so + c * t.scs];
-      else v = Ar<T>::neg(src[so + c * t.scs]);
-      dst[d + c * t.dcs] = v;
+      else if (t.sign > 0) v = base[so + c * t.scs];
+      else v = Ar<T>::neg(base[so + c * t.scs]);
+      base[d + c * t.dcs] = v;
     }
   }
 }
@@ -158,11 +193,10 @@ __global__ void __launch_bounds__(256) k_copy_tags(const DTag* __restrict__ tags
 // Red-black Gauss-Seidel half-sweep: cells with (i+j+k) mod 2 == color (global indices)
 // take phi = (s - h^2 rhs) / 6.  Lane l of a warp updates cells par + 2l (+64 k) of a line.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_rbgs_half(const DRow* __restrict__ rows, int nbox,
-                                                        long long nrows, long long per, int color) {
+__global__ void __launch_bounds__(kThreads) k_rbgs_half(SegList L, long long nrows, long long per,
+                                                        int color) {
   const int lane = threadIdx.x & 31;
-  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
-    const DRow& R = rows[b];
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)(lr % n1), z = (int)(lr / n1);
     const DView vp = R.v[0];
@@ -177,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_half(const DRow* __restrict__
   });
 }
 
-// Flush per-warp maxima: each warp stores (solve, max); thread 0 merges equal solves.
+// Flush per-warp maxima: each warp stores (slot, max); thread 0 merges equal slots.
 __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
                                                 unsigned long long* norms) {
   __shared__ unsigned long long s_max[kWarps];
@@ -202,22 +236,22 @@ __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
   }
 }
 
-// Residual r = rhs - (s - 6 phi) * (1/h^2), optionally stored, with a fused max-norm.
+// Residual r = rhs - (s - 6 phi) / h^2, optionally stored, with a fused max-norm into
+// norms[slot + solve].
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_residual(const DRow* __restrict__ rows, int nbox,
-                                                       long long nrows, long long per,
+__global__ void __launch_bounds__(kThreads) k_residual(SegList L, long long nrows, long long per,
                                                        unsigned long long* norms) {
   const int lane = threadIdx.x & 31;
   unsigned long long mx = 0;
   int cur = -1;
-  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
-    const DRow& R = rows[b];
-    if (R.solve != cur) {
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
+    const int idx = slot + R.solve;
+    if (idx != cur) {
       if (cur >= 0 && norms) {
         unsigned long long m = Ar<T>::key_to_f64bits(warp_max(mx));
         if (lane == 0 && m) atomicMax(&norms[cur], m);
       }
-      cur = R.solve;
+      cur = idx;
       mx = 0;
     }
     const int n0 = R.n[0], n1 = R.n[1];
@@ -241,12 +275,10 @@ __global__ void __launch_bounds__(kThreads) k_residual(const DRow* __restrict__ 
 // Fused residual + restriction.  Lane l of a warp produces coarse cells X = l, l+32, ... of
 // one coarse x-line: the 8 child residuals summed x fastest, times 1/8.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_residual_restrict(const DRow* __restrict__ rows,
-                                                                int nbox, long long nrows,
+__global__ void __launch_bounds__(kThreads) k_residual_restrict(SegList L, long long nrows,
                                                                 long long per) {
   const int lane = threadIdx.x & 31;
-  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
-    const DRow& R = rows[b];
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int nc0 = R.n[0] >> 1, nc1 = R.n[1] >> 1;
     const int Y = (int)(lr % nc1), Z = (int)(lr / nc1);
     const DView vp = R.v[0], vr = R.v[1];
@@ -274,11 +306,9 @@ __global__ void __launch_bounds__(kThreads) k_residual_restrict(const DRow* __re
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_restrict(const DRow* __restrict__ rows, int nbox,
-                                                       long long nrows, long long per) {
+__global__ void __launch_bounds__(kThreads) k_restrict(SegList L, long long nrows, long long per) {
   const int lane = threadIdx.x & 31;
-  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
-    const DRow& R = rows[b];
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int nc0 = R.n[0] >> 1, nc1 = R.n[1] >> 1;
     const int Y = (int)(lr % nc1), Z = (int)(lr / nc1);
     T* c = line<T>(R.c[0], Y, Z);
@@ -300,11 +330,9 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const DRow* __restrict__ 
 
 // fine(c) += coarse(floor(c / 2)); c[0] addresses coarse cell floor(lo / 2).
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_prolong_add(const DRow* __restrict__ rows, int nbox,
-                                                          long long nrows, long long per) {
+__global__ void __launch_bounds__(kThreads) k_prolong_add(SegList L, long long nrows, long long per) {
   const int lane = threadIdx.x & 31;
-  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
-    const DRow& R = rows[b];
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)(lr % n1), z = (int)(lr / n1);
     const int ox = R.lo[0] & 1, oy = R.lo[1] & 1, oz = R.lo[2] & 1;
@@ -315,11 +343,10 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(const DRow* __restrict
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_set_valid(const DRow* __restrict__ rows, int nbox,
-                                                        long long nrows, long long per, T value) {
+__global__ void __launch_bounds__(kThreads) k_set_valid(SegList L, long long nrows, long long per,
+                                                        T value) {
   const int lane = threadIdx.x & 31;
-  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
-    const DRow& R = rows[b];
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)(lr % n1), z = (int)(lr / n1);
     T* f = line<T>(R.v[0], y, z);
@@ -351,14 +378,12 @@ __global__ void k_bottom(const BottomJob* __restrict__ jobs) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_dense_copy(const DRow* __restrict__ rows, int nbox,
-                                                         long long nrows, long long per, T* dense,
-                                                         int3 dlo, int3 dn, int ncomp,
+__global__ void __launch_bounds__(kThreads) k_dense_copy(SegList L, long long nrows, long long per,
+                                                         T* dense, int3 dlo, int3 dn, int ncomp,
                                                          int to_dense) {
   const int lane = threadIdx.x & 31;
   const long long dplane = (long long)dn.x * dn.y, dcomp = dplane * dn.z;
-  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
-    const DRow& R = rows[b];
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)(lr % n1), z = (int)(lr / n1);
     T* f = line<T>(R.v[0], y, z);
@@ -377,20 +402,19 @@ __global__ void __launch_bounds__(kThreads) k_dense_copy(const DRow* __restrict_
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_maxabs(const DRow* __restrict__ rows, int nbox,
-                                                     long long nrows, long long per,
+__global__ void __launch_bounds__(kThreads) k_maxabs(SegList L, long long nrows, long long per,
                                                      unsigned long long* norms) {
   const int lane = threadIdx.x & 31;
   unsigned long long mx = 0;
   int cur = -1;
-  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
-    const DRow& R = rows[b];
-    if (R.solve != cur) {
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
+    const int idx = slot + R.solve;
+    if (idx != cur) {
       if (cur >= 0) {
         unsigned long long m = Ar<T>::key_to_f64bits(warp_max(mx));
         if (lane == 0 && m) atomicMax(&norms[cur], m);
       }
-      cur = R.solve;
+      cur = idx;
       mx = 0;
     }
     const int n0 = R.n[0], n1 = R.n[1];
@@ -404,20 +428,18 @@ __global__ void __launch_bounds__(kThreads) k_maxabs(const DRow* __restrict__ ro
   flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
 }
 
-__device__ __forceinline__ double norm_of(const unsigned long long* norms, int solve) {
-  return __longlong_as_double((long long)norms[solve]);
+__device__ __forceinline__ double norm_of(const unsigned long long* norms, int idx) {
+  return __longlong_as_double((long long)norms[idx]);
 }
 // 2^e with 2^e <= s < 2^(e+1), and its inverse; both exact powers of two
 __device__ __forceinline__ double pow2_floor(double s) { return ldexp(1.0, ilogb(s)); }
 __device__ __forceinline__ double pow2_floor_inv(double s) { return ldexp(1.0, -ilogb(s)); }
 
-__global__ void __launch_bounds__(kThreads) k_residual_scale_f32(const DRow* __restrict__ rows,
-                                                                 int nbox, long long nrows,
+__global__ void __launch_bounds__(kThreads) k_residual_scale_f32(SegList L, long long nrows,
                                                                  long long per,
                                                                  const unsigned long long* norms) {
   const int lane = threadIdx.x & 31;
-  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
-    const DRow& R = rows[b];
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)(lr % n1), z = (int)(lr / n1);
     const DView vp = R.v[0];
@@ -425,7 +447,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_scale_f32(const DRow* __r
     const double* rhs = line<double>(R.v[1], y, z);
     float* r32 = line<float>(R.c[0], y, z);
     const double ih2 = R.ih2;
-    const double down = pow2_floor_inv(norm_of(norms, R.solve));
+    const double down = pow2_floor_inv(norm_of(norms, slot + R.solve));
     for (int x = lane; x < n0; x += 32) {
       double s = nbr_sum(phi + x, vp.pitch, vp.plane);
       double v = residual_of(s, phi[x], rhs[x], ih2);
@@ -434,17 +456,15 @@ __global__ void __launch_bounds__(kThreads) k_residual_scale_f32(const DRow* __r
   });
 }
 
-__global__ void __launch_bounds__(kThreads) k_correct_add(const DRow* __restrict__ rows, int nbox,
-                                                          long long nrows, long long per,
+__global__ void __launch_bounds__(kThreads) k_correct_add(SegList L, long long nrows, long long per,
                                                           const unsigned long long* norms) {
   const int lane = threadIdx.x & 31;
-  for_rows(rows, nbox, nrows, per, [&](int b, long long lr) {
-    const DRow& R = rows[b];
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)(lr % n1), z = (int)(lr / n1);
     double* phi = line<double>(R.v[0], y, z);
     const float* e = line<float>(R.c[0], y, z);
-    const double up = pow2_floor(norm_of(norms, R.solve));
+    const double up = pow2_floor(norm_of(norms, slot + R.solve));
     for (int x = lane; x < n0; x += 32) phi[x] = __fma_rn(up, (double)e[x], phi[x]);
   });
 }
@@ -481,63 +501,129 @@ int num_sms() {
   return n;
 }
 
-cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int nchunks,
-                             void* const* bases, int ncomp, cudaStream_t s) {
+#define GB_DISPATCH(dt, KERNEL, GRID, BLOCK, SMEM, STREAM, ...)                       \
+  do {                                                                                 \
+    if ((dt) == DT_F64) KERNEL<double><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);    \
+    else KERNEL<float><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);                    \
+  } while (0)
+
+cudaError_t launch_copy_tags_l(int dt, const TagList& L, long long nchunks, int ncomp, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
   unsigned blocks = (unsigned)((nchunks + 7) / 8);
-  if (dt == DT_F64) k_copy_tags<double><<<blocks, 256, 0, s>>>(tags, chunks, nchunks, bases, ncomp);
-  else k_copy_tags<float><<<blocks, 256, 0, s>>>(tags, chunks, nchunks, bases, ncomp);
+  GB_DISPATCH(dt, k_copy_tags, blocks, 256, 0, s, L, nchunks, ncomp);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
-                             cudaStream_t s) {
+cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int nchunks, void* base,
+                             int ncomp, cudaStream_t s) {
+  TagList L{};
+  L.one.tags = tags;
+  L.one.chunks = chunks;
+  L.one.base = base;
+  L.one.chunk_begin = 0;
+  L.one.nchunks = nchunks;
+  L.n = 1;
+  return launch_copy_tags_l(dt, L, nchunks, ncomp, s);
+}
+
+cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int color, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   Grid g = row_grid(nrows, 16);
-  if (dt == DT_F64) k_rbgs_half<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, color);
-  else k_rbgs_half<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, color);
+  GB_DISPATCH(dt, k_rbgs_half, g.blocks, kThreads, 0, s, L, nrows, g.per, color);
   count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
+                              cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 4);
+  GB_DISPATCH(dt, k_residual, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  GB_DISPATCH(dt, k_residual_restrict, g.blocks, kThreads, 0, s, L, nrows, g.per);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  GB_DISPATCH(dt, k_prolong_add, g.blocks, kThreads, 0, s, L, nrows, g.per);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_valid_l(int dt, const SegList& L, long long nrows, double value, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  if (dt == DT_F64) k_set_valid<double><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, value);
+  else k_set_valid<float><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, (float)value);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxabs_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
+                            cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 4);
+  GB_DISPATCH(dt, k_maxabs, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_scale_f32_l(const SegList& L, long long nrows,
+                                        const unsigned long long* norms, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  k_residual_scale_f32<<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsigned long long* norms,
+                                 cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  k_correct_add<<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---- single-table launchers (one segment) ------------------------------------------------
+
+cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
+                             cudaStream_t s) {
+  return launch_rbgs_half_l(dt, one_seg(rows, nbox), nrows, color, s);
 }
 
 cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
                             unsigned long long* norms, cudaStream_t s) {
-  if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 4);
-  if (dt == DT_F64) k_residual<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
-  else k_residual<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
-  count_launches(1);
-  return cudaGetLastError();
+  return launch_residual_l(dt, one_seg(rows, nbox), nrows, norms, s);
 }
 
 cudaError_t launch_residual_restrict(int dt, const DRow* rows, int nbox, long long nrows,
                                      cudaStream_t s) {
-  if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 16);
-  if (dt == DT_F64) k_residual_restrict<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
-  else k_residual_restrict<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
-  count_launches(1);
-  return cudaGetLastError();
+  return launch_residual_restrict_l(dt, one_seg(rows, nbox), nrows, s);
 }
 
 cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   Grid g = row_grid(nrows, 16);
-  if (dt == DT_F64) k_restrict<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
-  else k_restrict<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
+  GB_DISPATCH(dt, k_restrict, g.blocks, kThreads, 0, s, one_seg(rows, nbox), nrows, g.per);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prolong_add(int dt, const DRow* rows, int nbox, long long nrows,
                                cudaStream_t s) {
-  if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 16);
-  if (dt == DT_F64) k_prolong_add<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
-  else k_prolong_add<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per);
-  count_launches(1);
-  return cudaGetLastError();
+  return launch_prolong_add_l(dt, one_seg(rows, nbox), nrows, s);
 }
 
 cudaError_t launch_bottom(int dt, const BottomJob* jobs, int njobs, int maxN, cudaStream_t s) {
@@ -552,12 +638,7 @@ cudaError_t launch_bottom(int dt, const BottomJob* jobs, int njobs, int maxN, cu
 
 cudaError_t launch_set_valid(int dt, const DRow* rows, int nbox, long long nrows, double value,
                              cudaStream_t s) {
-  if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 16);
-  if (dt == DT_F64) k_set_valid<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, value);
-  else k_set_valid<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, (float)value);
-  count_launches(1);
-  return cudaGetLastError();
+  return launch_set_valid_l(dt, one_seg(rows, nbox), nrows, value, s);
 }
 
 cudaError_t launch_set_flat(int dt, void* p, long long n, double value, cudaStream_t s) {
@@ -579,39 +660,26 @@ cudaError_t launch_dense_copy(int dt, const DRow* rows, int nbox, long long nrow
   int3 lo = make_int3(dom_lo[0], dom_lo[1], dom_lo[2]);
   int3 n = make_int3(dom_n[0], dom_n[1], dom_n[2]);
   if (dt == DT_F64)
-    k_dense_copy<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, (double*)dense, lo, n, ncomp, to_dense);
+    k_dense_copy<double><<<g.blocks, kThreads, 0, s>>>(one_seg(rows, nbox), nrows, g.per, (double*)dense, lo, n, ncomp, to_dense);
   else
-    k_dense_copy<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, (float*)dense, lo, n, ncomp, to_dense);
+    k_dense_copy<float><<<g.blocks, kThreads, 0, s>>>(one_seg(rows, nbox), nrows, g.per, (float*)dense, lo, n, ncomp, to_dense);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_maxabs(int dt, const DRow* rows, int nbox, long long nrows,
                           unsigned long long* norms, cudaStream_t s) {
-  if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 4);
-  if (dt == DT_F64) k_maxabs<double><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
-  else k_maxabs<float><<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
-  count_launches(1);
-  return cudaGetLastError();
+  return launch_maxabs_l(dt, one_seg(rows, nbox), nrows, norms, s);
 }
 
 cudaError_t launch_residual_scale_f32(const DRow* rows, int nbox, long long nrows,
                                       const unsigned long long* norms, cudaStream_t s) {
-  if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 16);
-  k_residual_scale_f32<<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
-  count_launches(1);
-  return cudaGetLastError();
+  return launch_residual_scale_f32_l(one_seg(rows, nbox), nrows, norms, s);
 }
 
 cudaError_t launch_correct_add(const DRow* rows, int nbox, long long nrows,
                                const unsigned long long* norms, cudaStream_t s) {
-  if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 16);
-  k_correct_add<<<g.blocks, kThreads, 0, s>>>(rows, nbox, nrows, g.per, norms);
-  count_launches(1);
-  return cudaGetLastError();
+  return launch_correct_add_l(one_seg(rows, nbox), nrows, norms, s);
 }
 
 }  // namespace gbmg

@@ -39,9 +39,9 @@ struct DRow {
   DView c[2];    // op-specific coarse views, addressing coarse cell floor(lo/2)
 };
 
-// Ghost-fill / dense-copy tag: destination cells dst + x + y*dsy + z*dsz (0 <= x < ex ...)
-// take sign * src[src + x*ssx + y*ssy + z*ssz]; components at +c*dcs / +c*scs.  Offsets are
-// in elements from bases[base_dst] / bases[base_src].  sign 0 writes 0.
+// Ghost-fill tag: destination cells dst + x + y*dsy + z*dsz (0 <= x < ex ...) take
+// sign * base[src + x*ssx + y*ssy + z*ssz]; components at +c*dcs / +c*scs.  Offsets are in
+// elements from the fab's base address.  sign 0 writes 0.
 struct DTag {
   long long src, dst;
   long long scs, dcs;
@@ -49,8 +49,7 @@ struct DTag {
   int dsy, dsz;
   int ex, ey, ez;
   int sign;
-  int base_src, base_dst;
-  int pad_;
+  int pad_[3];
 };
 
 // Exact bottom solve of one level: phi[off_phi[i]] = sum_j Mt[j*N + i] * rhs[off_rhs[j]].
@@ -66,6 +65,59 @@ struct BottomJob {
 
 constexpr int kTagChunk = 128;  // destination cells per warp in the copy-tag kernel
 
+// A launch may cover the box tables of several independent solves (batched and served
+// solves): each solve's table is one segment of the launch's row space.  norms and scales
+// of a row live at index slot + DRow::solve.
+struct Seg {
+  const DRow* rows;
+  long long row_begin;  // first launch row of this segment
+  int nbox;
+  int slot;
+};
+struct SegList {
+  const Seg* segs;  // device array, used when n > 1
+  Seg one;          // the segment when n == 1
+  int n;
+};
+inline SegList one_seg(const DRow* rows, int nbox, int slot = 0) {
+  SegList L{};
+  L.one.rows = rows;
+  L.one.row_begin = 0;
+  L.one.nbox = nbox;
+  L.one.slot = slot;
+  L.n = 1;
+  return L;
+}
+
+// Copy tags of one fab (offsets relative to base) in a fill launch covering several fabs.
+struct TagSeg {
+  const DTag* tags;
+  const int2* chunks;
+  void* base;
+  long long chunk_begin;
+  int nchunks;
+  int pad_;
+};
+struct TagList {
+  const TagSeg* segs;
+  TagSeg one;
+  int n;
+};
+
+// Tiles of one solve's level in a fused-sweep launch covering several solves.
+struct UnitSeg {
+  const DRow* rows;
+  const int2* units;
+  long long unit_begin;
+  int nunits;
+  int pad_;
+};
+struct UnitList {
+  const UnitSeg* segs;
+  UnitSeg one;
+  int n;
+};
+
 int num_sms();
 
 // Process-wide count of kernels enqueued by the launchers below (plus graph kernel nodes
@@ -74,7 +126,7 @@ void count_launches(long long n);
 long long launches_so_far();
 
 cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int nchunks,
-                             void* const* bases, int ncomp, cudaStream_t s);
+                             void* base, int ncomp, cudaStream_t s);
 
 // v[0] = phi (ghosts filled), v[1] = rhs.
 cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
@@ -131,5 +183,23 @@ cudaError_t launch_residual_scale_f32(const DRow* rows, int nbox, long long nrow
 // v[0] = phi (FP64), c[0] = e (FP32 view, same geometry): phi = phi + s * double(e).
 cudaError_t launch_correct_add(const DRow* rows, int nbox, long long nrows,
                                const unsigned long long* norms, cudaStream_t s);
+
+// Launchers over segment lists (several solves per launch); nrows / nchunks / nunits are
+// the totals over all segments.
+cudaError_t launch_copy_tags_l(int dt, const TagList& L, long long nchunks, int ncomp, cudaStream_t s);
+cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int color, cudaStream_t s);
+cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
+                              cudaStream_t s);
+cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s);
+cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cudaStream_t s);
+cudaError_t launch_set_valid_l(int dt, const SegList& L, long long nrows, double value, cudaStream_t s);
+cudaError_t launch_maxabs_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
+                            cudaStream_t s);
+cudaError_t launch_residual_scale_f32_l(const SegList& L, long long nrows,
+                                        const unsigned long long* norms, cudaStream_t s);
+cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsigned long long* norms,
+                                 cudaStream_t s);
+cudaError_t launch_rbgs_fused_l(int dt, const UnitList& L, long long nunits, int ty, int depth,
+                                int max_pitch, int max_pitch_r, int* err, cudaStream_t s);
 
 }  // namespace gbmg

@@ -171,20 +171,21 @@ std::vector<DTag> device_tags(const BoxArray& ba, const FabLayout& lay,
     d.ey = t.ext[1];
     d.ez = t.ext[2];
     d.sign = t.sign;
-    d.base_src = d.base_dst = base_index;
+    (void)base_index;
     out.push_back(d);
   }
   return out;
 }
 
-FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc) {
+FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc, int layers) {
   int per[3];
-  int key = bc_code(bc, per);
+  const int ng = (layers < 0 || layers > f.lay.g) ? f.lay.g : layers;
+  int key = bc_code(bc, per) + 8 * ng;
   auto it = f.fills.find(key);
   if (it != f.fills.end()) return *it->second;
   std::vector<CopyTag> tags;
   std::string err;
-  if (!make_copy_tags(f.ba->ba, per, f.lay.g, &tags, &err)) fail(MG_EINVAL, err);
+  if (!make_copy_tags(f.ba->ba, per, ng, &tags, &err)) fail(MG_EINVAL, err);
   std::unique_ptr<FillPlan> P(new FillPlan);
   P->host_tags = device_tags(f.ba->ba, f.lay, tags, 0);
   std::vector<int2> chunks;
@@ -198,19 +199,17 @@ FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc) {
     P->tags = c.upload(P->host_tags.data(), P->host_tags.size() * sizeof(DTag), c.stream);
     P->chunks = c.upload(chunks.data(), chunks.size() * sizeof(int2), c.stream);
   }
-  void* bases[1] = {f.base};
-  P->bases = c.upload(bases, sizeof bases, c.stream);
   MG_CK(cudaStreamSynchronize(c.stream));
   FillPlan& ref = *P;
   f.fills[key] = std::move(P);
   return ref;
 }
 
-void launch_fill(Ctx& c, FabObj& f, const mg_bc* bc, cudaStream_t s) {
-  FillPlan& P = fill_plan(c, f, bc);
+void launch_fill(Ctx& c, FabObj& f, const mg_bc* bc, cudaStream_t s, int layers) {
+  FillPlan& P = fill_plan(c, f, bc, layers);
   if (!P.nchunks) return;
   MG_CK(launch_copy_tags(f.dtype, (const DTag*)P.tags->p, (const int2*)P.chunks->p, P.nchunks,
-                         (void* const*)P.bases->p, f.lay.ncomp, s));
+                         f.base, f.lay.ncomp, s));
 }
 
 OpTable upload_table(Ctx& c, const std::vector<DRow>& rows, long long nrows, cudaStream_t s) {
@@ -448,6 +447,16 @@ DView coarse_view(const FabObj& coarse, int cb, const Box& fine_box) {
 extern "C" {
 
 int mg_version(void) { return 1; }
+
+int mg_pool_info(mg_ctx_t h, size_t* cap, size_t* in_use) {
+  return guard([&] {
+    Ctx* c = (Ctx*)h;
+    if (!c) fail(MG_EINVAL, "ctx is NULL");
+    if (cap) *cap = c->pool_cap;
+    if (in_use) *in_use = c->in_use.load();
+    return MG_OK;
+  });
+}
 
 int mg_kernel_launches(int64_t* n) {
   if (!n) return MG_EINVAL;
@@ -760,7 +769,6 @@ int mg_fab_free(mg_ctx_t h, mg_fab_t fab, void* stream) {
     for (auto& kv : f->fills) {
       kv.second->tags ? kv.second->tags->reset(s) : void();
       kv.second->chunks ? kv.second->chunks->reset(s) : void();
-      kv.second->bases ? kv.second->bases->reset(s) : void();
     }
     if (f->valid_rows) f->valid_rows->reset(s);
     if (f->own) f->own->reset(s);

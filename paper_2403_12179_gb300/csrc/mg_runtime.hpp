@@ -77,7 +77,7 @@ struct BoxArrayObj {
 // A ghost-fill plan: device copy tags + chunk list for one fab and one set of BCs.
 struct FillPlan {
   std::vector<DTag> host_tags;  // offsets relative to the fab base (base index 0)
-  DevBufP tags, chunks, bases;
+  DevBufP tags, chunks;
   int nchunks = 0;
 };
 
@@ -120,6 +120,7 @@ struct Ctx {
   int64_t next_id = 1;
   std::chrono::steady_clock::time_point t0;
   std::vector<std::shared_ptr<Hierarchy>> hier;   // cached solver hierarchies
+  std::recursive_mutex hier_mu;                    // guards hier (scheduler thread + callers)
   std::map<std::string, std::vector<double>> bottom_cache;  // key -> transposed M
   // device error word written by kernels whose bounded waits expire (0 = fine)
   DevBufP d_err;
@@ -155,8 +156,9 @@ struct Ctx {
 int bc_code(const mg_bc* bc, int periodic[3]);  // validates; returns a small cache key
 
 // Plans and tables ----------------------------------------------------------------------
-FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc);
-void launch_fill(Ctx& c, FabObj& f, const mg_bc* bc, cudaStream_t s);
+// Ghost fill of the first `layers` ghost layers (-1: all of the fab's layers).
+FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc, int layers = -1);
+void launch_fill(Ctx& c, FabObj& f, const mg_bc* bc, cudaStream_t s, int layers = -1);
 void ensure_valid_rows(Ctx& c, FabObj& f);
 
 // Appends one row per box of `ba` to a host table; views(b, row) fills the views of box b.

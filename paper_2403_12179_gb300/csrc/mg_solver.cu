@@ -12,6 +12,7 @@
 #include <cstring>
 
 #include "mg_runtime.hpp"
+#include "mg_solver.hpp"
 
 namespace gbmg {
 
@@ -52,41 +53,6 @@ DView coarse_view_of(const FabObj& coarse, const Box& fine_box) {
 }
 
 }  // namespace
-
-struct LevelData {
-  std::shared_ptr<BoxArrayObj> bao;
-  double h = 1.0;
-  std::shared_ptr<FabObj> phi, rhs;
-  OpTable smooth, rr, prolong, zero;
-  // fused sweeps ping-pong between phi and phi2 (same layout)
-  bool fused = false;
-  std::shared_ptr<FabObj> phi2;
-  FusedTable f_ab, f_ba;
-};
-
-struct Hierarchy {
-  // cache key
-  int64_t rhs_id = 0, phi_id = 0;
-  int bc_key = 0;
-  SolveParams p;
-  mg_bc bc{};
-  int dt = DT_F64;  // inner precision
-  bool mixed = false;
-  std::vector<LevelData> L;
-  std::shared_ptr<FabObj> phi0, rhs0;  // the caller's fabs (FP64)
-  OpTable resid0, rhsabs0, scale0, correct0, zero0_64;
-  DevBufP Mt, offr, offp, job;
-  int N = 0;
-  DevBufP dnorm;  // [0] residual norm bits, [1] rhs norm bits
-  unsigned long long* hnorm = nullptr;
-  cudaGraphExec_t step_graph = nullptr;
-  cudaStream_t graph_stream = nullptr;
-  long long graph_kernels = 0;
-  ~Hierarchy() {
-    if (step_graph) cudaGraphExecDestroy(step_graph);
-    if (hnorm) cudaFreeHost(hnorm);
-  }
-};
 
 namespace {
 
@@ -173,18 +139,23 @@ void build_tables(Ctx& c, Hierarchy& H, cudaStream_t s) {
   J.phi = B.phi->base;
   J.N = (int)N;
   H.job = c.upload(&J, sizeof J, s);
+  H.job_host = J;
   // fill plans must exist before any graph capture
   for (auto& D : H.L) {
-    fill_plan(c, *D.phi, &H.bc);
+    fill_plan(c, *D.phi, &H.bc, 1);
     if (D.fused) {
+      fill_plan(c, *D.phi, &H.bc);
       fill_plan(c, *D.phi2, &H.bc);
       fill_plan(c, *D.rhs, &H.bc);
     }
   }
-  fill_plan(c, *H.phi0, &H.bc);
+  fill_plan(c, *H.phi0, &H.bc, 1);
 }
 
+}  // namespace
+
 Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, const SolveParams& p) {
+  std::lock_guard<std::recursive_mutex> lk(c.hier_mu);
   int per[3];
   int key = bc_code(bc, per);
   for (auto& h : c.hier) {
@@ -250,6 +221,8 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
   return *c.hier.back();
 }
 
+namespace {
+
 void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s) {
   int k = 0;
   if (D.fused) {
@@ -263,7 +236,7 @@ void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s) {
   }
   for (; k < sweeps; ++k)
     for (int color = 0; color < 2; ++color) {
-      launch_fill(c, *D.phi, &H.bc, s);
+      launch_fill(c, *D.phi, &H.bc, s, 1);  // the 7-point half-sweep reads one layer
       MG_CK(launch_rbgs_half(H.dt, D.smooth.rows(), D.smooth.nbox, D.smooth.nrows, color, s));
     }
 }
@@ -274,7 +247,7 @@ void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s) {
     LevelData& D = H.L[l];
     if (D.fused) launch_fill(c, *D.rhs, &H.bc, s);  // rhs ghosts for the redundant ring
     smooth(c, H, D, H.p.nu1, s);
-    launch_fill(c, *D.phi, &H.bc, s);
+    launch_fill(c, *D.phi, &H.bc, s, 1);
     MG_CK(launch_residual_restrict(H.dt, D.rr.rows(), D.rr.nbox, D.rr.nrows, s));
   }
   MG_CK(launch_bottom(H.dt, (const BottomJob*)H.job->p, 1, H.N, s));
@@ -298,7 +271,7 @@ void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
   if (H.mixed)
     MG_CK(launch_correct_add(H.correct0.rows(), H.correct0.nbox, H.correct0.nrows, dn, s));
   MG_CK(cudaMemsetAsync(dn, 0, 8, s));
-  launch_fill(c, *H.phi0, &H.bc, s);
+  launch_fill(c, *H.phi0, &H.bc, s, 1);
   MG_CK(launch_residual(DT_F64, H.resid0.rows(), H.resid0.nbox, H.resid0.nrows, dn, s));
   MG_CK(cudaMemcpyAsync(H.hnorm, dn, 16, cudaMemcpyDeviceToHost, s));
 }
@@ -346,6 +319,7 @@ double bits_to_double(unsigned long long b) {
 }  // namespace
 
 void drop_hierarchies_of(Ctx& c, int64_t fab_id) {
+  std::lock_guard<std::recursive_mutex> lk(c.hier_mu);
   bool any = false;
   for (auto& h : c.hier)
     if (h->rhs_id == fab_id || h->phi_id == fab_id) any = true;
@@ -357,7 +331,10 @@ void drop_hierarchies_of(Ctx& c, int64_t fab_id) {
   c.hier.swap(keep);
 }
 
-void destroy_hierarchies(Ctx& c) { c.hier.clear(); }
+void destroy_hierarchies(Ctx& c) {
+  std::lock_guard<std::recursive_mutex> lk(c.hier_mu);
+  c.hier.clear();
+}
 
 int solve(Ctx& c, int64_t rhs_id, int64_t phi_id, const mg_bc* bc, double tol,
           const SolveParams& p, mg_result* res) {
@@ -372,7 +349,7 @@ int solve(Ctx& c, int64_t rhs_id, int64_t phi_id, const mg_bc* bc, double tol,
   // ||rhs||_inf and the first residual norm
   MG_CK(cudaMemsetAsync(dn, 0, 16, s));
   MG_CK(launch_maxabs(DT_F64, H.rhsabs0.rows(), H.rhsabs0.nbox, H.rhsabs0.nrows, dn, s));
-  launch_fill(c, *H.phi0, bc, s);
+  launch_fill(c, *H.phi0, bc, s, 1);
   MG_CK(launch_residual(DT_F64, H.resid0.rows(), H.resid0.nbox, H.resid0.nrows, dn, s));
   MG_CK(cudaMemcpyAsync(H.hnorm, dn, 16, cudaMemcpyDeviceToHost, s));
   MG_CK(cudaStreamSynchronize(s));
@@ -413,25 +390,6 @@ int solve(Ctx& c, int64_t rhs_id, int64_t phi_id, const mg_bc* bc, double tol,
   return status;
 }
 
-int solve_batch(Ctx& c, int n, const int64_t* rhs, const int64_t* phi, const mg_bc* bcs,
-                double tol, const SolveParams& p, mg_result* res) {
-  (void)c; (void)n; (void)rhs; (void)phi; (void)bcs; (void)tol; (void)p; (void)res;
-  fail(MG_EINVAL, "batched solve not built yet");
-}
-
-int server_submit(Ctx& c, int64_t rhs, int64_t phi, const mg_bc* bc, double tol,
-                  const SolveParams& p, int64_t* ticket) {
-  (void)c; (void)rhs; (void)phi; (void)bc; (void)tol; (void)p; (void)ticket;
-  fail(MG_EINVAL, "serving not built yet");
-}
-
-int server_poll(Ctx& c, int64_t ticket, int timeout_ms, mg_result* res) {
-  (void)c; (void)ticket; (void)timeout_ms; (void)res;
-  fail(MG_EINVAL, "serving not built yet");
-}
-
-void server_stop(Ctx& c) { (void)c; }
-
 }  // namespace gbmg
 
 using namespace gbmg;
@@ -456,6 +414,7 @@ int mg_solve_batch(mg_ctx_t h, int n, const mg_fab_t* rhs, const mg_fab_t* phi, 
     if (!c || n <= 0 || !rhs || !phi || !bcs) fail(MG_EINVAL, "bad argument");
     auto f = c->get_fab(phi[0]);
     SolveParams p = params_from(opt, f->ba->ba);
+    if (!(opt && opt->h > 0)) p.h = 0.0;  // resolved per solve from its own domain
     return solve_batch(*c, n, rhs, phi, bcs, tol, p, res);
   });
 }

@@ -127,6 +127,16 @@ def mg_version():
     return lib().mg_version()
 
 
+def mg_pool_info(ctx):
+    cap, used = ctx_size(), ctx_size()
+    _ck(lib().mg_pool_info(ctx, ctypes.byref(cap), ctypes.byref(used)))
+    return cap.value, used.value
+
+
+def ctx_size():
+    return ctypes.c_size_t()
+
+
 def mg_set_stream(ctx, stream):
     _ck(lib().mg_set_stream(ctx, _s(stream)))
 

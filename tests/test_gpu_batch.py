@@ -1,0 +1,180 @@
+"""Batched solves (one launch per V-cycle stage for many solves) and the serving loop
+(continuous batching via mg_submit / mg_poll): every result must equal, bit for bit, the
+same problem solved alone with mg_solve, whatever company it had."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_12179_gb300 import inputs, mg
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+PROBLEMS = [(32, 16, (1, 1, 1)), (24, 8, (0, 0, 0)), (16, 16, (1, 0, 1)), (48, 16, (0, 0, 0)),
+            (8, 8, (1, 1, 1)), (32, 32, (0, 1, 0)), (2, 2, (0, 0, 0))]
+
+
+@pytest.fixture(scope="module")
+def gctx():
+    import paper_2403_12179_gb300.build as b
+    b.build()
+    assert torch.cuda.is_available()
+    ctx = mg.mg_init(0)
+    yield ctx
+    mg.mg_finalize(ctx)
+
+
+def _rhs(n, periodic, seed):
+    r = inputs.rng(seed).standard_normal((n, n, n))
+    return inputs.remove_mean(r) if all(periodic) else r
+
+
+def _make(ctx, n, box, periodic, seed, ng=(2, 1)):
+    ba = mg.mg_box_array_create(ctx, (0, 0, 0), (n - 1,) * 3, (box,) * 3)
+    rhs = _rhs(n, periodic, seed)
+    fr = gu.dense_fab(ctx, ba, rhs, ng[1])
+    fp = mg.mg_fab_alloc(ctx, ba, 1, ng[0])
+    return rhs, fr, fp
+
+
+def _alone(ctx, n, box, periodic, seed, precision):
+    rhs, fr, fp = _make(ctx, n, box, periodic, seed)
+    res = mg.mg_solve(ctx, fr, fp, mg.make_bc(periodic), 1e-10, mg.make_options(precision=precision))
+    phi = gu.fab_dense(ctx, fp, rhs.shape)
+    mg.mg_fab_free(ctx, fr)
+    mg.mg_fab_free(ctx, fp)
+    return phi, res
+
+
+@pytest.mark.parametrize("precision", [mg.MG_PREC_F64, mg.MG_PREC_MIXED])
+def test_batch_equals_alone_bitwise(gctx, precision):
+    alone = [_alone(gctx, n, b, p, 100 + i, precision) for i, (n, b, p) in enumerate(PROBLEMS)]
+    made = [_make(gctx, n, b, p, 100 + i) for i, (n, b, p) in enumerate(PROBLEMS)]
+    res = mg.mg_solve_batch(gctx, [m[1] for m in made], [m[2] for m in made],
+                            [mg.make_bc(p) for (_, _, p) in PROBLEMS], 1e-10,
+                            mg.make_options(precision=precision))
+    for (rhs, fr, fp), r, (phi_a, res_a) in zip(made, res, alone):
+        assert r.status == mg.MG_OK and res_a.status == mg.MG_OK
+        assert r.vcycles == res_a.vcycles and r.rel_resid <= 1e-10
+        assert np.array_equal(gu.fab_dense(gctx, fp, rhs.shape), phi_a)
+    for _, fr, fp in made:
+        mg.mg_fab_free(gctx, fr)
+        mg.mg_fab_free(gctx, fp)
+
+
+def test_batch_reports_each_status(gctx):
+    made = [_make(gctx, 16, 8, (0, 0, 0), 120), _make(gctx, 16, 8, (0, 0, 0), 121)]
+    rhs_bad = made[1][0].copy()
+    rhs_bad[3, 4, 5] = np.nan
+    t = torch.from_numpy(rhs_bad).cuda()
+    mg.mg_fab_copy_from_dense(gctx, made[1][1], t.data_ptr(), False)
+    torch.cuda.synchronize()
+    res = mg.mg_solve_batch(gctx, [m[1] for m in made], [m[2] for m in made],
+                            [mg.make_bc((0, 0, 0))] * 2, 1e-10)
+    assert res[0].status == mg.MG_OK and res[1].status == mg.MG_ENAN
+
+
+def _serve(ctx, specs, precision, timeout_ms=-1):
+    made, tickets = [], []
+    for i, (n, b, p) in enumerate(specs):
+        m = _make(ctx, n, b, p, 200 + i)
+        made.append(m)
+        tickets.append(mg.mg_submit(ctx, m[1], m[2], mg.make_bc(p), 1e-10,
+                                    mg.make_options(precision=precision)))
+    out = []
+    for t in tickets:
+        rc, r = mg.mg_poll(ctx, t, timeout_ms)
+        assert rc == mg.MG_OK
+        out.append(r)
+    return made, out
+
+
+@pytest.mark.parametrize("precision", [mg.MG_PREC_F64, mg.MG_PREC_MIXED])
+def test_serving_results_equal_alone(precision):
+    ctx = mg.mg_init(0)
+    actx = mg.mg_init(0)
+    try:
+        specs = PROBLEMS * 2
+        made, res = _serve(ctx, specs, precision)
+        for i, ((n, b, p), (rhs, fr, fp), r) in enumerate(zip(specs, made, res)):
+            assert r.status == mg.MG_OK and r.rel_resid <= 1e-10
+            assert r.t_end >= r.t_admit >= r.t_start and r.seconds > 0
+            phi = gu.fab_dense(ctx, fp, rhs.shape)
+            phi_a, res_a = _alone(actx, n, b, p, 200 + i, precision)
+            assert res_a.vcycles == r.vcycles
+            assert np.array_equal(phi, phi_a)
+    finally:
+        mg.mg_finalize(ctx)
+        mg.mg_finalize(actx)
+
+
+def _wrapped_problem(ctx, n, box, per, seed, keep):
+    ba = mg.mg_box_array_create(ctx, (0, 0, 0), (n - 1,) * 3, (box,) * 3)
+    rhs = _rhs(n, per, seed)
+    out = []
+    for ng in (1, 2):
+        nb = mg.mg_fab_layout(ctx, ba, 1, ng, mg.MG_F64)
+        t = torch.zeros(nb // 8 + 64, dtype=torch.float64, device="cuda")
+        ptr = t.data_ptr() + (-t.data_ptr()) % 256
+        keep.append(t)
+        out.append(mg.mg_fab_wrap(ctx, ba, 1, ng, mg.MG_F64, ptr, nb))
+    fr, fp = out
+    t = torch.from_numpy(rhs).cuda()
+    mg.mg_fab_copy_from_dense(ctx, fr, t.data_ptr(), False)
+    torch.cuda.synchronize()
+    return rhs, fr, fp
+
+
+def test_serving_admission_under_small_pool():
+    """The pool holds the coarse levels of about two solves at a time: later requests wait
+    for running solves to retire, and every result equals the solve alone."""
+    n, box, per = 64, 32, (0, 0, 0)
+    keep = []
+    # bytes one solve's hierarchy takes from the pool
+    probe = mg.mg_init(0)
+    try:
+        rhs, fr, fp = _wrapped_problem(probe, n, box, per, 299, keep)
+        _, before = mg.mg_pool_info(probe)
+        mg.mg_solve(probe, fr, fp, mg.make_bc(per), 1e-10)
+        _, after = mg.mg_pool_info(probe)
+    finally:
+        mg.mg_finalize(probe)
+    per_solve = after - before
+    assert per_solve > 0
+    ctx = mg.mg_init(0)
+    _, base = mg.mg_pool_info(ctx)
+    mg.mg_finalize(ctx)
+    ctx = mg.mg_init(0, base + int(2.5 * per_solve) + (1 << 20))
+    actx = mg.mg_init(0)
+    try:
+        made = [_wrapped_problem(ctx, n, box, per, 300 + i, keep) for i in range(8)]
+        tickets = [mg.mg_submit(ctx, fr, fp, mg.make_bc(per), 1e-10) for (_, fr, fp) in made]
+        res = [mg.mg_poll(ctx, t, -1)[1] for t in tickets]
+        assert all(r.status == mg.MG_OK for r in res)
+        first_end = min(r.t_end for r in res)
+        assert sum(r.t_admit >= first_end for r in res) >= 4   # admitted only after retirements
+        for i, ((rhs, fr, fp), r) in enumerate(zip(made, res)):
+            phi = gu.fab_dense(ctx, fp, rhs.shape)
+            phi_a, res_a = _alone(actx, n, box, per, 300 + i, mg.MG_PREC_F64)
+            assert np.array_equal(phi, phi_a) and res_a.vcycles == r.vcycles
+    finally:
+        mg.mg_finalize(ctx)
+        mg.mg_finalize(actx)
+
+
+def test_poll_paths():
+    ctx = mg.mg_init(0)
+    try:
+        with pytest.raises(mg.MgError):
+            mg.mg_poll(ctx, 12345, 0)
+        rhs, fr, fp = _make(ctx, 128, 64, (0, 0, 0), 400)
+        t = mg.mg_submit(ctx, fr, fp, mg.make_bc((0, 0, 0)), 1e-10)
+        rc, _ = mg.mg_poll(ctx, t, 0)
+        assert rc in (mg.MG_PENDING, mg.MG_OK)
+        if rc == mg.MG_PENDING:
+            rc, r = mg.mg_poll(ctx, t, -1)
+            assert rc == mg.MG_OK and r.status == mg.MG_OK
+        with pytest.raises(mg.MgError):
+            mg.mg_poll(ctx, t, 0)            # a ticket is released once reported
+    finally:
+        mg.mg_finalize(ctx)
