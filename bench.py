@@ -262,6 +262,27 @@ def run_ours(args, wl_name):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if prec == mg.MG_PREC_MIXED:
+        # the plain FP64 path on the same problem: time and the difference of the answers
+        # (P7: two answers that both meet tol differ by at most 2 * 0.06 * tol * ||rhs||)
+        fp64 = mg.mg_fab_alloc(ctx, ba, 1, 2)
+        opt64 = mg.make_options()
+        mg.mg_solve(ctx, fr, fp64, bc, 1e-10, opt64)
+        t64 = []
+        for _ in range(2):
+            mg.mg_fab_set_val(ctx, fp64, 0.0, True, stream)
+            stream.synchronize()
+            t = time.perf_counter()
+            r64 = mg.mg_solve(ctx, fr, fp64, bc, 1e-10, opt64)
+            t64.append(time.perf_counter() - t)
+        a = _fab_to_dense(ctx, fp, (n,) * 3, stream)
+        b = _fab_to_dense(ctx, fp64, (n,) * 3, stream)
+        diff = float((a - b).abs().max())
+        del a, b
+        line["vs_f64"] = {"f64_ms_per_solve": round(min(t64) * 1e3, 3), "f64_vcycles": r64.vcycles,
+                          "max_abs_diff": diff,
+                          "p7_bound": 2 * 0.06 * 1e-10 * float(np.abs(rhs_np).max())}
+        mg.mg_fab_free(ctx, fp64, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl_name, vcycles)
     mg.mg_finalize(ctx)
@@ -374,6 +395,227 @@ def run_kernels_only(args, wl_name):
     print(json.dumps({"kernels_only": wl_name, "launch_s": kt}))
 
 
+# ---- other workloads: batched, serving, mixed vs FP64, ghost-fill microbench ----------------
+
+def _dense_to_fab(ctx, ba, dense_dev, ng, stream=None):
+    from paper_2403_12179_gb300 import mg
+    fab = mg.mg_fab_alloc(ctx, ba, 1, ng)
+    mg.mg_fab_copy_from_dense(ctx, fab, dense_dev.data_ptr(), False, stream)
+    return fab
+
+
+def _fab_to_dense(ctx, fab, shape, stream=None):
+    import torch
+    from paper_2403_12179_gb300 import mg
+    out = torch.empty(shape, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    mg.mg_fab_copy_to_dense(ctx, fab, out.data_ptr(), False, stream)
+    if stream is not None:
+        stream.synchronize()
+    torch.cuda.synchronize()
+    return out
+
+
+def run_batched(args):
+    """512 independent periodic problems (edges from {32,48,64,96,128}, 32^3 boxes): all
+    packed into one launch per V-cycle stage, FP64 and mixed; against the same problems
+    solved one at a time with mg_solve (FP64)."""
+    import numpy as np
+    import torch
+    from paper_2403_12179_gb300 import inputs, mg
+    probs = inputs.batched_periodic(args.count, seed=4)
+    ctx = mg.mg_init(0)
+    stream = torch.cuda.Stream()
+    mg.mg_set_stream(ctx, stream)
+    fr, fp, shapes = [], [], []
+    for pb in probs:
+        ba = mg.mg_box_array_create(ctx, (0, 0, 0), (pb.n - 1,) * 3, (pb.box,) * 3)
+        d = torch.from_numpy(pb.rhs()).cuda()
+        fr.append(_dense_to_fab(ctx, ba, d, 1, stream))
+        fp.append(mg.mg_fab_alloc(ctx, ba, 1, 2))
+        shapes.append((pb.n,) * 3)
+    stream.synchronize()
+    bcs = [mg.make_bc((1, 1, 1))] * len(probs)
+    cells = sum(pb.n ** 3 for pb in probs)
+
+    def batch(prec):
+        for f in fp:
+            mg.mg_fab_set_val(ctx, f, 0.0, True, stream)
+        t = time.perf_counter()
+        res = mg.mg_solve_batch(ctx, fr, fp, bcs, 1e-10, mg.make_options(precision=prec))
+        dt = time.perf_counter() - t
+        assert all(r.status == 0 and r.rel_resid <= 1e-10 for r in res), "batched solve failed"
+        return dt, res
+
+    out = {}
+    for name, prec in (("mixed", mg.MG_PREC_MIXED), ("f64", mg.MG_PREC_F64)):
+        for _ in range(max(1, args.warmup)):
+            batch(prec)
+        ts = [batch(prec)[0] for _ in range(args.steps)]
+        out[name] = statistics.median(ts)
+    phis64 = [_fab_to_dense(ctx, f, sh, stream) for f, sh in zip(fp, shapes)]
+    batch(mg.MG_PREC_MIXED)
+    diff = 0.0
+    for f, sh, p64 in zip(fp, shapes, phis64):
+        pm = _fab_to_dense(ctx, f, sh, stream)
+        d = (pm - pm.mean()) - (p64 - p64.mean())
+        diff = max(diff, float(d.abs().max()))
+    # one solve at a time, FP64, same problems
+    seq = []
+    for f in fp:
+        mg.mg_fab_set_val(ctx, f, 0.0, True, stream)
+    for a, b in zip(fr, fp):                       # warm: hierarchies and graphs exist
+        mg.mg_solve(ctx, a, b, bcs[0], 1e-10)
+    for f in fp:
+        mg.mg_fab_set_val(ctx, f, 0.0, True, stream)
+    stream.synchronize()
+    t = time.perf_counter()
+    for a, b in zip(fr, fp):
+        r = mg.mg_solve(ctx, a, b, bcs[0], 1e-10)
+        seq.append(r.vcycles)
+    t_seq = time.perf_counter() - t
+    n = len(probs)
+    line = {"metric": f"solves/s, {n} batched periodic problems to 1e-10 (mixed precision)",
+            "value": round(n / out["mixed"], 2), "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(out["mixed"] * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner / f64 outer", "data": "synthetic",
+            "config": {"workload": "batched512", "problems": n, "cells": cells,
+                       "edges": "32/48/64/96/128 (seed 4)", "box": 32},
+            "f64_batched_solves_per_s": round(n / out["f64"], 2),
+            "f64_one_at_a_time_solves_per_s": round(n / t_seq, 2),
+            "cell_updates_per_s_mixed": round(cells * 8 * 9 / out["mixed"], 1),
+            "max_abs_diff_mixed_vs_f64_mod_const": diff}
+    mg.mg_finalize(ctx)
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Poisson arrivals (200/s), edges {32,64,128,256} p={.4,.3,.2,.1}, periodic/Dirichlet,
+    32^3 or 64^3 boxes: real-time replay through mg_submit/mg_poll (mixed precision,
+    continuous batching), against a one-at-a-time FP64 server (mg_solve in arrival order,
+    latencies from measured service times)."""
+    import threading
+    import numpy as np
+    import torch
+    from paper_2403_12179_gb300 import inputs, mg
+    reqs = inputs.serving_requests(args.requests, seed=6)
+    ctx = mg.mg_init(0)
+    fabs = []
+    gen = torch.Generator(device="cuda")
+    for rq in reqs:
+        ba = mg.mg_box_array_create(ctx, (0, 0, 0), (rq.n - 1,) * 3, (rq.box,) * 3)
+        gen.manual_seed(rq.seed)
+        d = torch.randn((rq.n,) * 3, dtype=torch.float64, device="cuda", generator=gen)
+        if rq.periodic:
+            d -= d.mean()
+        fr = _dense_to_fab(ctx, ba, d, 1)
+        fp = mg.mg_fab_alloc(ctx, ba, 1, 2)
+        fabs.append((fr, fp, mg.make_bc((1, 1, 1) if rq.periodic else (0, 0, 0))))
+    torch.cuda.synchronize()
+    opt = mg.make_options(precision=mg.MG_PREC_MIXED)
+    results = [None] * len(reqs)
+    tickets = [None] * len(reqs)
+    ready = threading.Semaphore(0)
+
+    def poller():
+        for i in range(len(reqs)):
+            ready.acquire()
+            rc, r = mg.mg_poll(ctx, tickets[i], -1)
+            results[i] = r
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for i, rq in enumerate(reqs):
+        delay = t0 + rq.t_arrive - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        fr, fp, bc = fabs[i]
+        tickets[i] = mg.mg_submit(ctx, fr, fp, bc, 1e-10, opt)
+        ready.release()
+    th.join()
+    wall = max(r.t_end for r in results) - min(r.t_start for r in results)
+    lat = np.array([r.seconds for r in results]) * 1e3
+    ok = all(r.status == 0 and r.rel_resid <= 1e-10 for r in results)
+    stats = mg.mg_server_stats_get(ctx)
+    mg.mg_finalize(ctx)
+    # one-at-a-time FP64 server on the same requests
+    ctx = mg.mg_init(0)
+    svc = []
+    for i, rq in enumerate(reqs):
+        ba = mg.mg_box_array_create(ctx, (0, 0, 0), (rq.n - 1,) * 3, (rq.box,) * 3)
+        gen.manual_seed(rq.seed)
+        d = torch.randn((rq.n,) * 3, dtype=torch.float64, device="cuda", generator=gen)
+        if rq.periodic:
+            d -= d.mean()
+        fr = _dense_to_fab(ctx, ba, d, 1)
+        fp = mg.mg_fab_alloc(ctx, ba, 1, 2)
+        bc = mg.make_bc((1, 1, 1) if rq.periodic else (0, 0, 0))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = mg.mg_solve(ctx, fr, fp, bc, 1e-10)
+        svc.append(time.perf_counter() - t)
+        ok = ok and r.status == 0
+        mg.mg_fab_free(ctx, fr)
+        mg.mg_fab_free(ctx, fp)
+    mg.mg_finalize(ctx)
+    end, lat64 = 0.0, []
+    for rq, sv in zip(reqs, svc):
+        start = max(rq.t_arrive, end)
+        end = start + sv
+        lat64.append((end - rq.t_arrive) * 1e3)
+    lat64 = np.array(lat64)
+    wall64 = end - reqs[0].t_arrive
+    n = len(reqs)
+    line = {"metric": f"served solves/s and latency, {n} Poisson-arrival requests at 200/s",
+            "value": round(n / wall, 2), "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner / f64 outer", "data": "synthetic (torch Philox rhs per request seed)",
+            "config": {"workload": "serving", "requests": n, "rate_per_s": 200,
+                       "edges": "32/64/128/256 p=.4/.3/.2/.1", "bc": "periodic/Dirichlet 50/50",
+                       "box": "32 or 64"},
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2),
+                           "p99": round(float(np.percentile(lat, 99)), 2)},
+            "all_converged_to_1e-10": ok, "scheduler": stats,
+            "f64_one_at_a_time": {"solves_per_s": round(n / wall64, 2),
+                                  "latency_ms": {"p50": round(float(np.percentile(lat64, 50)), 2),
+                                                 "p99": round(float(np.percentile(lat64, 99)), 2)},
+                                  "mean_service_ms": round(float(np.mean(svc)) * 1e3, 3)}}
+    print(json.dumps(line), flush=True)
+
+
+def run_fill(args):
+    """FillBoundary microbench: 256^3 periodic, 64 boxes of 64^3, 4 FP64 components, 2 ghost
+    layers; one fill kernel per call."""
+    import torch
+    from paper_2403_12179_gb300 import inputs, mg
+    ctx = mg.mg_init(0)
+    stream = torch.cuda.Stream()
+    ba = mg.mg_box_array_create(ctx, (0, 0, 0), (255,) * 3, (64,) * 3)
+    fab = mg.mg_fab_alloc(ctx, ba, 4, 2)
+    d = torch.from_numpy(inputs.fill_microbench(256, seed=3)).cuda()
+    mg.mg_fab_copy_from_dense(ctx, fab, d.data_ptr(), False, stream)
+    bc = mg.make_bc((1, 1, 1))
+    for _ in range(args.warmup):
+        mg.mg_fill_boundary(ctx, fab, bc, stream)
+    t = _time(stream, lambda k: mg.mg_fill_boundary(ctx, fab, bc, stream), args.steps * 10)
+    ghost = 64 * (68 ** 3 - 64 ** 3)
+    nbytes = ghost * 4 * 8 * 2
+    peaks, src = load_peaks()
+    ach = nbytes / t / 1e9
+    line = {"metric": "FillBoundary time per fill (256^3, 64 boxes, 4 comps, 2 ghosts, periodic)",
+            "value": round(t * 1e6, 2), "unit": "us", "n_gpus": 1, "steps": args.steps * 10,
+            "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fill", "ghost_cells": ghost, "bytes_per_fill": nbytes},
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
+                         "peak_source": src}}
+    mg.mg_finalize(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def mg_launches():
     import ctypes
     from paper_2403_12179_gb300 import mg
@@ -466,14 +708,23 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dirichlet256", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="dirichlet256",
+                    choices=sorted(WORKLOADS) + ["batched512", "serving", "fill"])
+    ap.add_argument("--count", type=int, default=512, help="problems in batched512")
+    ap.add_argument("--requests", type=int, default=1000, help="requests in serving")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time only the fine-level kernels (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.kernels_only:
+    if args.workload == "batched512":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
+    elif args.workload == "fill":
+        run_fill(args)
+    elif args.kernels_only:
         run_kernels_only(args, args.workload)
     elif args.impl == "reference":
         run_reference(args, args.workload)

@@ -301,6 +301,17 @@ int mg_solve_batch(mg_ctx_t ctx, int n, const mg_fab_t* rhs, const mg_fab_t* phi
 int mg_submit(mg_ctx_t ctx, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, double tol,
               const mg_options* opt, mg_ticket_t* out);
 
+/* Serving statistics since the scheduler started (no counterpart in the paper). */
+typedef struct {
+  int64_t submitted, admitted, completed, steps;
+  int64_t max_active;        /* largest number of solves in flight at once */
+  double admit_seconds;      /* host time building hierarchies of admitted requests */
+  double plan_seconds;       /* host time building and uploading per-step launch lists */
+  double step_seconds;       /* time from a step's first launch to its norms on the host */
+  double retire_seconds;     /* host time releasing finished solves */
+} mg_server_stats;
+int mg_server_stats_get(mg_ctx_t ctx, mg_server_stats* out);
+
 /* Wait up to timeout_ms (0: do not wait, -1: forever) for a ticket.  Returns MG_OK with
  * *res filled when done (the ticket is then released), MG_PENDING if not done in time,
  * MG_EINVAL for an unknown ticket. */

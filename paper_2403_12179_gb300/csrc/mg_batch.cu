@@ -23,6 +23,10 @@ namespace gbmg {
 
 namespace {
 
+double secs_since(std::chrono::steady_clock::time_point t) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t).count();
+}
+
 double bits2d(unsigned long long b) {
   double d;
   std::memcpy(&d, &b, 8);
@@ -66,15 +70,15 @@ struct TagB {
   long long total = 0;
   size_t off = 0;
   void add(const FillPlan& P, void* base) {
-    if (!P.nchunks) return;
+    if (!P.nchunks()) return;
     TagSeg s{};
-    s.tags = (const DTag*)P.tags->p;
-    s.chunks = (const int2*)P.chunks->p;
+    s.tags = P.tags();
+    s.chunks = P.chunks();
     s.base = base;
     s.chunk_begin = total;
-    s.nchunks = P.nchunks;
+    s.nchunks = P.nchunks();
     v.push_back(s);
-    total += P.nchunks;
+    total += P.nchunks();
   }
 };
 struct UnitB {
@@ -331,8 +335,14 @@ void finish(Ctx& c, Member& m) {
 
 // Runs one step for `run` (V-cycle) and `check` (norm check) members of one precision, reads
 // the norms back and applies the stop rule.
+struct StepTimes {
+  double plan = 0, step = 0;
+  long long steps = 0;
+};
+
 void step_and_decide(Ctx& c, Staging& st, std::vector<Member*>& run, std::vector<Member*>& check,
-                     int nslots, cudaStream_t s) {
+                     int nslots, cudaStream_t s, StepTimes* tm = nullptr) {
+  auto t0 = std::chrono::steady_clock::now();
   std::vector<Member*> fresh;
   for (Member* m : check)
     if (!m->started) fresh.push_back(m);
@@ -343,11 +353,17 @@ void step_and_decide(Ctx& c, Staging& st, std::vector<Member*>& run, std::vector
     S.mixed = check[0]->H->mixed;
   }
   upload_lists(c, S, st, s);
+  auto t1 = std::chrono::steady_clock::now();
   unsigned long long* norms = (unsigned long long*)c.d_norms->p;
   const size_t nbytes = (size_t)nslots * 8;
   enqueue_step(c, S, (const unsigned char*)st.dev->p, norms, nbytes, !fresh.empty(), s);
   MG_CK(cudaMemcpyAsync(c.h_norms, norms, nbytes, cudaMemcpyDeviceToHost, s));
   MG_CK(cudaStreamSynchronize(s));
+  if (tm) {
+    tm->plan += std::chrono::duration<double>(t1 - t0).count();
+    tm->step += secs_since(t1);
+    tm->steps += 1;
+  }
   check_device_error(c);
   for (Member* m : run) m->vcycles += 1;
   for (Member* m : check) {
@@ -430,7 +446,10 @@ struct Ctx::Server {
   std::thread th;
   size_t max_queue = 1 << 20;
   int max_active = 4096;
+  mg_server_stats stats{};
 };
+
+
 
 namespace {
 
@@ -456,6 +475,7 @@ void server_loop(Ctx* c) {
       }
     }
     std::vector<Member*> fresh_members;
+    auto t_admit0 = std::chrono::steady_clock::now();
     for (size_t k = 0; k < admit.size(); ++k) {
       const auto& r = admit[k];
       std::unique_ptr<Member> m(new Member);
@@ -495,6 +515,12 @@ void server_loop(Ctx* c) {
       fresh_members.push_back(m.get());
       active.push_back(std::move(m));
     }
+    {
+      std::lock_guard<std::mutex> lk(S.mu);
+      S.stats.admitted += (int64_t)fresh_members.size();
+      S.stats.admit_seconds += secs_since(t_admit0);
+      S.stats.max_active = std::max<int64_t>(S.stats.max_active, (int64_t)active.size());
+    }
     try {
       c->ensure_norm_slots(nslots);
       // one step per precision group: running members cycle, every member's norm is checked
@@ -505,7 +531,14 @@ void server_loop(Ctx* c) {
           check.push_back(m.get());
           if (m->started) run.push_back(m.get());
         }
-        if (!check.empty()) step_and_decide(*c, st, run, check, nslots, s);
+        if (!check.empty()) {
+          StepTimes tm;
+          step_and_decide(*c, st, run, check, nslots, s, &tm);
+          std::lock_guard<std::mutex> lk(S.mu);
+          S.stats.plan_seconds += tm.plan;
+          S.stats.step_seconds += tm.step;
+          S.stats.steps += tm.steps;
+        }
       }
     } catch (const MgError& e) {
       for (auto& m : active) {
@@ -514,6 +547,8 @@ void server_loop(Ctx* c) {
       }
     }
     // retire
+    auto t_ret0 = std::chrono::steady_clock::now();
+    int64_t ncomp = 0;
     std::vector<std::unique_ptr<Member>> keep;
     for (auto& m : active) {
       if (!m->done) {
@@ -534,9 +569,15 @@ void server_loop(Ctx* c) {
       }
       std::lock_guard<std::mutex> lk(S.mu);
       S.done[m->ticket] = m->res;
+      ++ncomp;
       S.cv_done.notify_all();
     }
     active.swap(keep);
+    {
+      std::lock_guard<std::mutex> lk(S.mu);
+      S.stats.completed += ncomp;
+      S.stats.retire_seconds += secs_since(t_ret0);
+    }
   }
   if (st.dev) st.dev->reset(s);
   cudaStreamSynchronize(s);
@@ -560,6 +601,7 @@ int server_submit(Ctx& c, int64_t rhs, int64_t phi, const mg_bc* bc, double tol,
   std::lock_guard<std::mutex> lk(S.mu);
   if (S.queue.size() >= S.max_queue) fail(MG_EAGAIN, "serving queue full");
   Ctx::Server::Req r{S.next_ticket++, rhs, phi, *bc, tol, p, c.now()};
+  S.stats.submitted += 1;
   S.known[r.ticket] = true;
   S.queue.push_back(r);
   *ticket = r.ticket;
@@ -580,6 +622,15 @@ int server_poll(Ctx& c, int64_t ticket, int timeout_ms, mg_result* res) {
   S.done.erase(ticket);
   S.known.erase(ticket);
   return MG_OK;
+}
+
+void server_stats(Ctx& c, mg_server_stats* out) {
+  if (!c.server) {
+    *out = mg_server_stats{};
+    return;
+  }
+  std::lock_guard<std::mutex> lk(c.server->mu);
+  *out = c.server->stats;
 }
 
 void server_stop(Ctx& c) {

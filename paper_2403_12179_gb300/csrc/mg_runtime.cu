@@ -180,26 +180,46 @@ std::vector<DTag> device_tags(const BoxArray& ba, const FabLayout& lay,
 FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc, int layers) {
   int per[3];
   const int ng = (layers < 0 || layers > f.lay.g) ? f.lay.g : layers;
-  int key = bc_code(bc, per) + 8 * ng;
+  const int code = bc_code(bc, per);
+  const int key = code + 8 * ng;
   auto it = f.fills.find(key);
   if (it != f.fills.end()) return *it->second;
-  std::vector<CopyTag> tags;
-  std::string err;
-  if (!make_copy_tags(f.ba->ba, per, ng, &tags, &err)) fail(MG_EINVAL, err);
+  // the pattern depends on the box array, BCs, layers filled and the fab layout only
+  const BoxArray& ba = f.ba->ba;
+  std::string tkey;
+  int hdr[6] = {code, ng, f.lay.g, f.lay.ncomp, f.esize(), (int)ba.boxes.size()};
+  tkey.append((const char*)hdr, sizeof hdr);
+  tkey.append((const char*)&ba.dom, sizeof(Box));
+  tkey.append((const char*)ba.boxes.data(), ba.boxes.size() * sizeof(Box));
+  std::shared_ptr<TagSet> set;
+  {
+    std::lock_guard<std::mutex> lk(c.tag_mu);
+    auto ct = c.tag_cache.find(tkey);
+    if (ct != c.tag_cache.end()) set = ct->second;
+  }
+  if (!set) {
+    std::vector<CopyTag> tags;
+    std::string err;
+    if (!make_copy_tags(ba, per, ng, &tags, &err)) fail(MG_EINVAL, err);
+    std::vector<DTag> dt = device_tags(ba, f.lay, tags, 0);
+    std::vector<int2> chunks;
+    for (size_t t = 0; t < dt.size(); ++t) {
+      int n = dt[t].ex * dt[t].ey * dt[t].ez;
+      for (int s0 = 0; s0 < n; s0 += kTagChunk) chunks.push_back(make_int2((int)t, s0));
+    }
+    set = std::make_shared<TagSet>();
+    set->nchunks = (int)chunks.size();
+    if (set->nchunks) {
+      set->tags_buf = c.upload(dt.data(), dt.size() * sizeof(DTag), c.stream);
+      set->chunks_buf = c.upload(chunks.data(), chunks.size() * sizeof(int2), c.stream);
+    }
+    // the pattern may be used on any stream from now on
+    MG_CK(cudaStreamSynchronize(c.stream));
+    std::lock_guard<std::mutex> lk(c.tag_mu);
+    c.tag_cache[tkey] = set;
+  }
   std::unique_ptr<FillPlan> P(new FillPlan);
-  P->host_tags = device_tags(f.ba->ba, f.lay, tags, 0);
-  std::vector<int2> chunks;
-  for (size_t t = 0; t < P->host_tags.size(); ++t) {
-    const DTag& d = P->host_tags[t];
-    int n = d.ex * d.ey * d.ez;
-    for (int s = 0; s < n; s += kTagChunk) chunks.push_back(make_int2((int)t, s));
-  }
-  P->nchunks = (int)chunks.size();
-  if (P->nchunks) {
-    P->tags = c.upload(P->host_tags.data(), P->host_tags.size() * sizeof(DTag), c.stream);
-    P->chunks = c.upload(chunks.data(), chunks.size() * sizeof(int2), c.stream);
-  }
-  MG_CK(cudaStreamSynchronize(c.stream));
+  P->set = set;
   FillPlan& ref = *P;
   f.fills[key] = std::move(P);
   return ref;
@@ -207,9 +227,8 @@ FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc, int layers) {
 
 void launch_fill(Ctx& c, FabObj& f, const mg_bc* bc, cudaStream_t s, int layers) {
   FillPlan& P = fill_plan(c, f, bc, layers);
-  if (!P.nchunks) return;
-  MG_CK(launch_copy_tags(f.dtype, (const DTag*)P.tags->p, (const int2*)P.chunks->p, P.nchunks,
-                         f.base, f.lay.ncomp, s));
+  if (!P.nchunks()) return;
+  MG_CK(launch_copy_tags(f.dtype, P.tags(), P.chunks(), P.nchunks(), f.base, f.lay.ncomp, s));
 }
 
 OpTable upload_table(Ctx& c, const std::vector<DRow>& rows, long long nrows, cudaStream_t s) {
@@ -232,6 +251,7 @@ void ensure_valid_rows(Ctx& c, FabObj& f) {
 
 const std::vector<double>& bottom_matrix_t(Ctx& c, const int n[3], const int periodic[3],
                                            double h) {
+  std::lock_guard<std::mutex> lk(c.bottom_mu);
   char key[160];
   std::snprintf(key, sizeof key, "%d,%d,%d,%d,%d,%d,%.17g", n[0], n[1], n[2], periodic[0],
                 periodic[1], periodic[2], h);
@@ -512,6 +532,7 @@ int mg_finalize(mg_ctx_t h) {
     c->op_cache.clear();
     c->fused_cache.clear();
     c->fabs.clear();
+    c->tag_cache.clear();
     c->bas.clear();
     c->d_norms.reset();
     c->d_err.reset();
@@ -765,10 +786,6 @@ int mg_fab_free(mg_ctx_t h, mg_fab_t fab, void* stream) {
       MG_CK(cudaEventRecord(ev, c->stream));
       MG_CK(cudaStreamWaitEvent(s, ev, 0));
       cudaEventDestroy(ev);
-    }
-    for (auto& kv : f->fills) {
-      kv.second->tags ? kv.second->tags->reset(s) : void();
-      kv.second->chunks ? kv.second->chunks->reset(s) : void();
     }
     if (f->valid_rows) f->valid_rows->reset(s);
     if (f->own) f->own->reset(s);

@@ -74,11 +74,20 @@ struct BoxArrayObj {
   const std::vector<BoxArray>& hierarchy();  // throws MG_EINVAL if no valid hierarchy
 };
 
-// A ghost-fill plan: device copy tags + chunk list for one fab and one set of BCs.
-struct FillPlan {
-  std::vector<DTag> host_tags;  // offsets relative to the fab base (base index 0)
-  DevBufP tags, chunks;
+// Device copy tags + chunk list of one ghost-fill pattern.  Offsets are relative to a fab's
+// base, so every fab with the same box array, ghost width, type and component count shares
+// one set (the cached communication pattern of Sec. 2).
+struct TagSet {
+  DevBufP tags_buf, chunks_buf;
   int nchunks = 0;
+};
+
+// A fab's ghost-fill plan for one set of BCs and number of layers.
+struct FillPlan {
+  std::shared_ptr<TagSet> set;
+  const DTag* tags() const { return set && set->tags_buf ? (const DTag*)set->tags_buf->p : nullptr; }
+  const int2* chunks() const { return set && set->chunks_buf ? (const int2*)set->chunks_buf->p : nullptr; }
+  int nchunks() const { return set ? set->nchunks : 0; }
 };
 
 struct FabObj {
@@ -135,6 +144,10 @@ struct Ctx {
   };
   std::map<std::string, CachedOp> op_cache;
   std::map<std::string, std::shared_ptr<struct FusedTable>> fused_cache;
+  // ghost-fill patterns shared by all fabs of one layout
+  std::mutex tag_mu;
+  std::map<std::string, std::shared_ptr<TagSet>> tag_cache;
+  std::mutex bottom_mu;  // guards bottom_cache
   // serving
   struct Server;
   std::shared_ptr<Server> server;
@@ -254,6 +267,7 @@ int server_submit(Ctx& c, int64_t rhs, int64_t phi, const mg_bc* bc, double tol,
                   const SolveParams& p, int64_t* ticket);
 int server_poll(Ctx& c, int64_t ticket, int timeout_ms, mg_result* res);
 void server_stop(Ctx& c);
+void server_stats(Ctx& c, mg_server_stats* out);
 
 // Bottom matrix (transposed), cached per (n, periodic, h).
 const std::vector<double>& bottom_matrix_t(Ctx& c, const int n[3], const int periodic[3],

@@ -215,7 +215,6 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
   }
   build_tables(c, *H, s);
   H->dnorm = c.alloc(16, s);
-  MG_CK(cudaMallocHost(&H->hnorm, 16));
   MG_CK(cudaStreamSynchronize(s));
   c.hier.push_back(std::move(H));
   return *c.hier.back();
@@ -345,6 +344,7 @@ int solve(Ctx& c, int64_t rhs_id, int64_t phi_id, const mg_bc* bc, double tol,
   double t_start = c.now();
   Hierarchy& H = get_hierarchy(c, *rhs, *phi, bc, p);
   cudaStream_t s = c.stream;
+  if (!H.hnorm) MG_CK(cudaMallocHost(&H.hnorm, 16));
   unsigned long long* dn = (unsigned long long*)H.dnorm->p;
   // ||rhs||_inf and the first residual norm
   MG_CK(cudaMemsetAsync(dn, 0, 16, s));
@@ -427,6 +427,15 @@ int mg_submit(mg_ctx_t h, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, double to
     auto f = c->get_fab(phi);
     SolveParams p = params_from(opt, f->ba->ba);
     return server_submit(*c, rhs, phi, bc, tol, p, out);
+  });
+}
+
+int mg_server_stats_get(mg_ctx_t h, mg_server_stats* out) {
+  return guard([&] {
+    Ctx* c = (Ctx*)h;
+    if (!c || !out) fail(MG_EINVAL, "NULL argument");
+    server_stats(*c, out);
+    return MG_OK;
   });
 }
 

@@ -360,6 +360,23 @@ def mg_submit(ctx, rhs, phi, bc, tol=1e-10, opt=None):
     return t.value
 
 
+class mg_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("max_active", ctypes.c_int64), ("admit_seconds", ctypes.c_double),
+                ("plan_seconds", ctypes.c_double), ("step_seconds", ctypes.c_double),
+                ("retire_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def mg_server_stats_get(ctx):
+    st = mg_server_stats()
+    _ck(lib().mg_server_stats_get(ctx, ctypes.byref(st)))
+    return st.as_dict()
+
+
 def mg_poll(ctx, ticket, timeout_ms=-1):
     """(rc, result): rc is MG_OK or MG_PENDING."""
     res = mg_result()
