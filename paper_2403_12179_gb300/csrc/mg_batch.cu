@@ -85,11 +85,11 @@ struct UnitB {
   std::vector<UnitSeg> v;
   long long total = 0;
   size_t off = 0;
-  int ty = 1, depth = 2, mp = 0, mpr = 0;
+  int ty = 1, depth = 3, mp = 0, mpr = 0;
   void add(const FusedTable& t) {
     UnitSeg s{};
     s.rows = t.rows.rows();
-    s.units = (const int2*)t.units->p;
+    s.units = (const int4*)t.units->p;
     s.unit_begin = total;
     s.nunits = t.nunits;
     v.push_back(s);

@@ -6,10 +6,11 @@
 //   * TMA bulk copies (cp.async.bulk, one per plane) bring phi rows [y0-2, y0+TY+2) and rhs
 //     rows [y0-1, y0+TY+1) of each plane into a ring of shared-memory buffers, completing on
 //     mbarriers; loads run D planes ahead of the compute;
-//   * stage s red-updates plane s over the tile plus a one-cell ring (the ring cells belong
+//   * a CTA owns planes [z0, z1) of its tile; stages z0-1 .. z1 each
+//     red-update plane s over the tile plus a one-cell ring (the ring cells belong
 //     to neighbouring tiles / boxes / periodic images and are recomputed redundantly from the
-//     second ghost layer -- exactly the values their owners compute), then black-updates
-//     plane s-1 using those red values;
+//     second ghost layer -- exactly the values their owners compute; planes z0-1 and z1 are
+//     recomputed the same way under the tile only), then black-updates plane s-1;
 //   * the finished plane s-1 goes back to global memory by one bulk store of whole rows into
 //     the destination buffer (a second phi allocation: tiles read each other's rows as
 //     halos, so the sweep cannot be done in place).
@@ -62,15 +63,21 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                "r"(bytes)
                : "memory");
 }
+// One try_wait that may suspend the thread for up to ~2 us while the phase is pending.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(2000u)
       : "memory");
   return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
@@ -96,11 +103,13 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-constexpr long long kSpinLimit = 1ll << 26;  // polls before a wait is declared stuck
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a wait this long is stuck
 
-// Bounded wait on one phase of an mbarrier.  Returns false on expiry.
+// Bounded wait on one phase of an mbarrier.  Returns false after kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (long long i = 0; i < kSpinLimit; ++i)
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (global_ns() - t0 < kWaitLimitNs)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -146,14 +155,14 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsi
 
   UnitSeg U = L.one;
   if (L.n > 1) U = L.segs[find_unitseg(L.segs, L.n, blockIdx.x)];
-  const int2 u = U.units[blockIdx.x - U.unit_begin];
+  const int4 u = U.units[blockIdx.x - U.unit_begin];  // box, y0, z0, z1
   const DRow& R = U.rows[u.x];
   Sweep<T> S;
   S.nx = R.n[0];
   S.ny = R.n[1];
   S.nz = R.n[2];
-  S.y0 = u.y;
-  S.ty = min(ty_max, S.ny - S.y0);
+  S.y0 = u.y & 0xFFFF;
+  S.ty = min(min(u.y >> 16, ty_max), S.ny - S.y0);
   S.pitch = R.v[0].pitch;
   S.plane = R.v[0].plane;
   S.g = R.v[0].g;
@@ -173,6 +182,7 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsi
   T* dst = (T*)R.v[2].p;              // valid cell (0,0,0) of the destination phi
   const int tid = threadIdx.x;
   const int nzl = S.nz;
+  const int z0 = u.z, z1 = u.w;  // this CTA finishes planes [z0, z1)
 
   if (tid == 0) {
     for (int i = 0; i < NP + NR; ++i) mbar_init(&bars[i], 1);
@@ -187,15 +197,15 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsi
   auto rhs_src = [&](int p) {
     return rhs + (long long)p * S.planer + (long long)(S.y0 - 1) * S.pr - S.gr;
   };
-  auto pslot = [&](int p) { return (p + 2 * NP) % NP; };  // p >= -2
-  auto rslot = [&](int p) { return (p + 2 * NR) % NR; };
-  // number of times a slot has been loaded before plane p (for the mbarrier parity)
-  auto pphase = [&](int p) { return (uint32_t)(((p + 2) / NP) & 1); };
-  auto rphase = [&](int p) { return (uint32_t)(((p + 1) / NR) & 1); };
+  // planes are loaded in order from z0-2 (phi) / z0-1 (rhs); slot and mbarrier parity
+  auto pslot = [&](int p) { return (p - z0 + 2) % NP; };
+  auto rslot = [&](int p) { return (p - z0 + 1) % NR; };
+  auto pphase = [&](int p) { return (uint32_t)(((p - z0 + 2) / NP) & 1); };
+  auto rphase = [&](int p) { return (uint32_t)(((p - z0 + 1) / NR) & 1); };
 
-  const int pmax = nzl + 1;  // last phi plane loaded
-  const int rmax = nzl;      // last rhs plane loaded
-  int p_issued = -3, r_issued = -2;  // last issued plane
+  const int pmax = z1 + 1;  // last phi plane loaded
+  const int rmax = z1;      // last rhs plane loaded
+  int p_issued = z0 - 3, r_issued = z0 - 2;  // last issued plane
   auto issue_phi = [&](int p) {
     if (p > pmax) return;
     uint64_t* b = &pbar[pslot(p)];
@@ -213,24 +223,60 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsi
 
   // Prologue: before stage s, phi planes up to s+D and rhs planes up to s+D-1 are queued.
   if (tid == 0) {
-    for (int p = -2; p <= -1 + D; ++p) issue_phi(p);
-    for (int p = -1; p <= -2 + D; ++p) issue_rhs(p);
+    for (int p = z0 - 2; p <= z0 - 1 + D; ++p) issue_phi(p);
+    for (int p = z0 - 1; p <= z0 - 2 + D; ++p) issue_rhs(p);
   }
 
+  // Lane mapping of a plane: lanes per row lpr = smallest power of two >= the row's
+  // x-pairs (at most 32); a warp covers 32 / lpr rows per pass, the 8 warps interleave.
+  const int npv = (S.nx + 1) >> 1;
+  int lsh = 0;
+  while ((1 << lsh) < npv && lsh < 5) ++lsh;
+  const int lpr = 1 << lsh;
+  const int plane_lane = (tid & 31) & (lpr - 1);
+  const int row0 = (tid >> 5) * (32 >> lsh) + ((tid & 31) >> lsh);
+  const int row_step = (blockDim.x >> 5) * (32 >> lsh);
+
+  __shared__ int s_ok;
   bool ok = true;
-  int p_done = -3, r_done = -2;  // planes every thread has seen land
-  for (int s = -1; s <= nzl; ++s) {
-    // Inputs of stage s: phi planes s-1..s+1 and rhs plane s (earlier planes landed in
-    // earlier stages).  Every thread waits on the barriers of the planes it reads.
-    for (int p = (s == -1 ? -2 : s + 1); p <= s + 1; ++p)
-      if (!mbar_wait_bounded(&pbar[pslot(p)], pphase(p))) ok = false;
-    if (!mbar_wait_bounded(&rbar[rslot(s)], rphase(s))) ok = false;
-    if (!__syncthreads_and(ok)) {
+  int p_done = z0 - 3, r_done = z0 - 2;  // planes thread 0 has seen land
+  auto store_plane = [&](int pb) {
+    // whole rows y0..y0+ty-1 of plane pb (x ghosts of the destination get overwritten;
+    // they are refilled before they are read)
+    T* gdst = dst + (long long)pb * S.plane + (long long)S.y0 * S.pitch - S.g;
+    bulk_store(gdst, pbuf + (size_t)pslot(pb) * phi_buf_elems + 2 * S.pitch,
+               (uint32_t)(S.ty * S.pitch * sizeof(T)));
+    bulk_commit();
+  };
+  for (int s = z0 - 1; s <= z1; ++s) {
+    // Thread 0 waits (bounded) for the inputs of stage s -- phi planes s-1..s+1 and rhs
+    // plane s -- while the other threads wait at the barrier instead of polling; after it,
+    // thread 0 stores plane s-2 (black-updated in the previous stage) and queues the loads
+    // for later stages into buffers whose stores have finished reading.
+    if (tid == 0) {
+      for (int p = (s == z0 - 1 ? z0 - 2 : s + 1); p <= s + 1; ++p)
+        if (!mbar_wait_bounded(&pbar[pslot(p)], pphase(p))) ok = false;
+      if (!mbar_wait_bounded(&rbar[rslot(s)], rphase(s))) ok = false;
+      if (ok) {
+        p_done = s + 1;
+        r_done = s;
+      }
+      s_ok = ok;
+    }
+    // every thread has finished stage s-1 (black plane s-2, fenced) and the inputs landed
+    __syncthreads();
+    if (!s_ok) {
       if (tid == 0) atomicExch(err, 1);
       break;
     }
-    p_done = s + 1;
-    r_done = s;
+    if (tid == 0) {
+      if (s - 2 >= z0) store_plane(s - 2);
+      bulk_wait_read1();  // the slot refilled below was stored two stages ago
+      if (s > z0 - 1) {
+        issue_phi(s + D);
+        issue_rhs(s + D - 1);
+      }
+    }
 
     T* P0 = pbuf + (size_t)pslot(s - 1) * phi_buf_elems;
     T* P1 = pbuf + (size_t)pslot(s) * phi_buf_elems;
@@ -240,86 +286,110 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsi
     const int gz = S.loz + s;
     // ---- red half of plane s
     {
-      bool ghost_plane = (s < 0 || s >= nzl);
-      bool skip = (s < 0 && (S.flags & 4)) || (s >= nzl && (S.flags & 32));
+      // planes outside [z0, z1) are needed only under the tile (z-neighbours of black cells)
+      const bool ghost_plane = (s < z0 || s >= z1);
+      const bool skip = (s < 0 && (S.flags & 4)) || (s >= nzl && (S.flags & 32));
       if (!skip) {
-        // rows / columns of the red region
         int ya = ghost_plane ? S.y0 : S.y0 - 1;
         int yb = ghost_plane ? S.y0 + S.ty - 1 : S.y0 + S.ty;
         if (!ghost_plane) {
           if (ya < 0 && (S.flags & 2)) ya = 0;
           if (yb >= S.ny && (S.flags & 16)) yb = S.ny - 1;
         }
-        int xa = ghost_plane ? 0 : -1, xb = ghost_plane ? S.nx - 1 : S.nx;
-        if (!ghost_plane) {
-          if (S.flags & 1) xa = 0;
-          if (S.flags & 8) xb = S.nx - 1;
+        // cells 0 <= x < nx of rows ya..yb: lanes cover (row, x-pair); pointers advance by
+        // whole rows, the red parity flips with each odd row step
+        int y = ya + row0;
+        if (y <= yb) {
+          const T* p0 = P0 + (y - S.y0 + 2) * S.pitch + S.g;
+          T* p1 = P1 + (y - S.y0 + 2) * S.pitch + S.g;
+          const T* p2 = P2 + (y - S.y0 + 2) * S.pitch + S.g;
+          const T* q = Q + (y - S.y0 + 1) * S.pr + S.gr;
+          int par = (S.lox + S.loy + y + gz) & 1;  // first red x >= 0 in row y
+          const int dstep = row_step * S.pitch, qstep = row_step * S.pr, pflip = row_step & 1;
+          for (; y <= yb; y += row_step) {
+            for (int x = par + 2 * plane_lane; x < S.nx; x += 2 * lpr) {
+              T* c = p1 + x;
+              T a = c[-1];
+              a = Ar<T>::add(a, c[1]);
+              a = Ar<T>::add(a, c[-S.pitch]);
+              a = Ar<T>::add(a, c[S.pitch]);
+              a = Ar<T>::add(a, p0[x]);
+              a = Ar<T>::add(a, p2[x]);
+              *c = gs_update(a, q[x], S.mh2);
+            }
+            p0 += dstep;
+            p1 += dstep;
+            p2 += dstep;
+            q += qstep;
+            par ^= pflip;
+          }
         }
-        const int nrow = yb - ya + 1;
-        const int npair = (xb - xa + 2) / 2;
-        for (int idx = tid; idx < nrow * npair; idx += blockDim.x) {
-          int y = ya + idx / npair;
-          int pr = idx % npair;
-          int gy = S.loy + y;
-          // first x >= xa with (lo + x + gy + gz) even
-          int x = xa + ((S.lox + xa + gy + gz) & 1) + 2 * pr;
-          if (x > xb) continue;
-          bool yin = y >= 0 && y < S.ny, xin = x >= 0 && x < S.nx;
-          if (!yin && !xin) continue;  // ring corner: not a neighbour of a tile cell
-          int o = (y - S.y0 + 2) * S.pitch + x + S.g;
-          T a = P1[o - 1];
-          a = Ar<T>::add(a, P1[o + 1]);
-          a = Ar<T>::add(a, P1[o - S.pitch]);
-          a = Ar<T>::add(a, P1[o + S.pitch]);
-          a = Ar<T>::add(a, P0[o]);
-          a = Ar<T>::add(a, P2[o]);
-          T q = Q[(y - S.y0 + 1) * S.pr + x + S.gr];
-          P1[o] = gs_update(a, q, S.mh2);
+        // ring cells x = -1 and x = nx of rows inside the box (their red value feeds the
+        // black update of x = 0 / nx-1), one thread per row
+        if (!ghost_plane) {
+          const bool lo_in = !(S.flags & 1), hi_in = !(S.flags & 8);
+          for (int y = ya + tid; y <= yb; y += blockDim.x) {
+            if (y < 0 || y >= S.ny) continue;
+            const int gy = S.loy + y;
+            const int orow = (y - S.y0 + 2) * S.pitch + S.g;
+            const int qrow = (y - S.y0 + 1) * S.pr + S.gr;
+            for (int side = 0; side < 2; ++side) {
+              const int x = side ? S.nx : -1;
+              if (!(side ? hi_in : lo_in) || ((S.lox + x + gy + gz) & 1)) continue;
+              const int o = orow + x;
+              T a = P1[o - 1];
+              a = Ar<T>::add(a, P1[o + 1]);
+              a = Ar<T>::add(a, P1[o - S.pitch]);
+              a = Ar<T>::add(a, P1[o + S.pitch]);
+              a = Ar<T>::add(a, P0[o]);
+              a = Ar<T>::add(a, P2[o]);
+              P1[o] = gs_update(a, Q[qrow + x], S.mh2);
+            }
+          }
         }
       }
     }
     __syncthreads();
-    // ---- black half of plane s-1 (tile cells only)
+    // ---- black half of plane s-1 (tile cells only); stored at the start of stage s+1
     const int pb = s - 1;
-    if (pb >= 0 && pb < nzl) {
+    if (pb >= z0 && pb < z1) {
       T* B0 = pbuf + (size_t)pslot(pb - 1) * phi_buf_elems;
       T* B1 = P0;
       T* B2 = P1;
       const T* QB = rbuf + (size_t)rslot(pb) * rhs_buf_elems;
       const int gzb = S.loz + pb;
-      const int npair = (S.nx + 1) / 2;
-      for (int idx = tid; idx < S.ty * npair; idx += blockDim.x) {
-        int y = S.y0 + idx / npair;
-        int pr = idx % npair;
-        int gy = S.loy + y;
-        int x = ((S.lox + gy + gzb + 1) & 1) + 2 * pr;
-        if (x >= S.nx) continue;
-        int o = (y - S.y0 + 2) * S.pitch + x + S.g;
-        T a = B1[o - 1];
-        a = Ar<T>::add(a, B1[o + 1]);
-        a = Ar<T>::add(a, B1[o - S.pitch]);
-        a = Ar<T>::add(a, B1[o + S.pitch]);
-        a = Ar<T>::add(a, B0[o]);
-        a = Ar<T>::add(a, B2[o]);
-        T q = QB[(y - S.y0 + 1) * S.pr + x + S.gr];
-        B1[o] = gs_update(a, q, S.mh2);
+      int y = S.y0 + row0;
+      if (y < S.y0 + S.ty) {
+        const T* b0 = B0 + (y - S.y0 + 2) * S.pitch + S.g;
+        T* b1 = B1 + (y - S.y0 + 2) * S.pitch + S.g;
+        const T* b2 = B2 + (y - S.y0 + 2) * S.pitch + S.g;
+        const T* q = QB + (y - S.y0 + 1) * S.pr + S.gr;
+        int par = (S.lox + S.loy + y + gzb + 1) & 1;  // first black x >= 0 in row y
+        const int dstep = row_step * S.pitch, qstep = row_step * S.pr, pflip = row_step & 1;
+        for (; y < S.y0 + S.ty; y += row_step) {
+          for (int x = par + 2 * plane_lane; x < S.nx; x += 2 * lpr) {
+            T* c = b1 + x;
+            T a = c[-1];
+            a = Ar<T>::add(a, c[1]);
+            a = Ar<T>::add(a, c[-S.pitch]);
+            a = Ar<T>::add(a, c[S.pitch]);
+            a = Ar<T>::add(a, b0[x]);
+            a = Ar<T>::add(a, b2[x]);
+            *c = gs_update(a, q[x], S.mh2);
+          }
+          b0 += dstep;
+          b1 += dstep;
+          b2 += dstep;
+          q += qstep;
+          par ^= pflip;
+        }
       }
-      fence_async_smem();
-    }
-    __syncthreads();
-    if (tid == 0) {
-      if (pb >= 0 && pb < nzl) {
-        // whole rows y0..y0+ty-1 of plane pb (x ghosts of the destination get overwritten;
-        // they are refilled before they are read)
-        T* gdst = dst + (long long)pb * S.plane + (long long)S.y0 * S.pitch - S.g;
-        bulk_store(gdst, P0 + 2 * S.pitch, (uint32_t)(S.ty * S.pitch * sizeof(T)));
-      }
-      bulk_commit();
-      bulk_wait_read1();  // the buffer reused below was stored two stages ago
-      issue_phi(s + 1 + D);
-      issue_rhs(s + D);
+      fence_async_smem();  // make the generic-proxy writes visible to the bulk store
     }
   }
+  // the last finished plane (z1-1) is stored after the loop
+  __syncthreads();
+  if (tid == 0 && s_ok && z1 - 1 >= z0) store_plane(z1 - 1);
   // Drain: wait (bounded) for every load this CTA issued but did not consume -- at most
   // D + 2 per ring, so each slot holds one outstanding phase -- and for the stores, so no
   // copy touches shared memory after the CTA exits.
@@ -368,13 +438,15 @@ cudaError_t launch_rbgs_fused_l(int dt, const UnitList& L, long long nunits, int
   if (nunits <= 0) return cudaSuccess;
   if (dt == DT_F64) {
     if (depth <= 1) return launch_fused_t<double, 1>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
-    return launch_fused_t<double, 2>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+    if (depth == 2) return launch_fused_t<double, 2>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+    return launch_fused_t<double, 3>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
   }
   if (depth <= 1) return launch_fused_t<float, 1>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
-  return launch_fused_t<float, 2>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+  if (depth == 2) return launch_fused_t<float, 2>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+  return launch_fused_t<float, 3>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
 }
 
-cudaError_t launch_rbgs_fused(int dt, const DRow* rows, const int2* units, int nunits, int ty,
+cudaError_t launch_rbgs_fused(int dt, const DRow* rows, const int4* units, int nunits, int ty,
                               int depth, int max_pitch, int max_pitch_r, int* err,
                               cudaStream_t s) {
   UnitList L{};

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) k_copy_tags(TagList L, long long nchunks,
 // Red-black Gauss-Seidel half-sweep: cells with (i+j+k) mod 2 == color (global indices)
 // take phi = (s - h^2 rhs) / 6.  Lane l of a warp updates cells par + 2l (+64 k) of a line.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_rbgs_half(SegList L, long long nrows, long long per,
+__global__ void __launch_bounds__(kThreads, 6) k_rbgs_half(SegList L, long long nrows, long long per,
                                                         int color) {
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
@@ -239,7 +239,7 @@ __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
 // Residual r = rhs - (s - 6 phi) / h^2, optionally stored, with a fused max-norm into
 // norms[slot + solve].
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_residual(SegList L, long long nrows, long long per,
+__global__ void __launch_bounds__(kThreads, 6) k_residual(SegList L, long long nrows, long long per,
                                                        unsigned long long* norms) {
   const int lane = threadIdx.x & 31;
   unsigned long long mx = 0;
@@ -538,7 +538,7 @@ cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int co
 cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
                               cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 4);
+  Grid g = row_grid(nrows, 16);
   GB_DISPATCH(dt, k_residual, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
   count_launches(1);
   return cudaGetLastError();

@@ -63,6 +63,25 @@ struct BottomJob {
   int pad_;
 };
 
+// The coarse end of a V-cycle (levels lc .. bottom) in one CTA: every level held densely in
+// shared memory (phi with one ghost layer, then rhs, x fastest), offsets in elements of the
+// level's type.  rows / nbox: level lc's box table (v[0] = phi, v[1] = rhs), through which
+// phi and rhs of level lc are gathered and phi is scattered back.
+constexpr int kMaxCoarseLevels = 8;
+struct CoarseLevel {
+  int n[3];   // level domain extents
+  int lo[3];  // level domain low corner (colour parity, gather offsets)
+  int off_phi, off_rhs;
+  double h2, ih2;
+};
+struct CoarseJob {
+  const DRow* rows;
+  const double* Mt;  // bottom (pseudo-)inverse, transposed, over the last level's cells
+  int nbox, nlev, nu1, nu2, N;
+  int periodic[3];
+  CoarseLevel lev[kMaxCoarseLevels];
+};
+
 constexpr int kTagChunk = 128;  // destination cells per warp in the copy-tag kernel
 
 // A launch may cover the box tables of several independent solves (batched and served
@@ -107,7 +126,7 @@ struct TagList {
 // Tiles of one solve's level in a fused-sweep launch covering several solves.
 struct UnitSeg {
   const DRow* rows;
-  const int2* units;
+  const int4* units;  // {box, y0, z0, z1}
   long long unit_begin;
   int nunits;
   int pad_;
@@ -152,13 +171,21 @@ cudaError_t launch_prolong_add(int dt, const DRow* rows, int nbox, long long nro
 // Fused red + black sweep (see mg_fused.cu).  Rows: v[0] = source phi (2 ghost layers,
 // filled), v[1] = rhs (1 ghost layer, filled), v[2] = destination phi with the source's
 // layout; pad_ = Dirichlet-face flags (bit d: low face of dim d, bit 3+d: high face).
-// units[i] = {box, y0} tiles of height ty; depth = planes loaded ahead (1 or 2).
+// units[i] = {box, y0, z0, z1}: rows [y0, y0+ty) x planes [z0, z1) of a box; depth = planes
+// loaded ahead (1 or 2).
 size_t fused_smem_bytes(int dt, int ty, int max_pitch, int max_pitch_r, int depth);
-cudaError_t launch_rbgs_fused(int dt, const DRow* rows, const int2* units, int nunits, int ty,
+cudaError_t launch_rbgs_fused(int dt, const DRow* rows, const int4* units, int nunits, int ty,
                               int depth, int max_pitch, int max_pitch_r, int* err,
                               cudaStream_t s);
 
 cudaError_t launch_bottom(int dt, const BottomJob* jobs, int njobs, int maxN, cudaStream_t s);
+
+// Shared memory of a coarse job whose levels have extents n[0..nlev); launch with the largest
+// value over the jobs.
+size_t coarse_smem_bytes(int dt, const int (*n)[3], int nlev);
+constexpr size_t kCoarseSmemMax = 200 * 1024;
+cudaError_t launch_coarse_cycle(int dt, const CoarseJob* jobs, int njobs, size_t smem,
+                                cudaStream_t s);
 
 // v[0] = field: valid cells = value.
 cudaError_t launch_set_valid(int dt, const DRow* rows, int nbox, long long nrows, double value,

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <cstdlib>
 #include <sstream>
 
 #include "mg_runtime.hpp"
@@ -109,6 +110,29 @@ void Ctx::ensure_norm_slots(int n) {
   d_norms = alloc((size_t)m * 8, stream);
   MG_CK(cudaMallocHost(&h_norms, (size_t)m * 8));
   norm_slots = m;
+}
+
+void Ctx::load_tune_file() {
+  if (tune_loaded) return;
+  tune_loaded = true;
+  const char* path = std::getenv("GBMG_TUNE_FILE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char key[200];
+  FusedCfg cfg;
+  while (std::fscanf(f, "%199s %d %d %d", key, &cfg.ty, &cfg.zc, &cfg.depth) == 4)
+    if (cfg.ty > 0 && cfg.zc > 0 && cfg.depth >= 1 && cfg.depth <= 3) tune[key] = cfg;
+  std::fclose(f);
+}
+
+void Ctx::save_tune_entry(const std::string& key, const FusedCfg& cfg) {
+  const char* path = std::getenv("GBMG_TUNE_FILE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %d\n", key.c_str(), cfg.ty, cfg.zc, cfg.depth);
+  std::fclose(f);
 }
 
 const std::vector<BoxArray>& BoxArrayObj::hierarchy() {
@@ -295,21 +319,22 @@ bool fused_eligible(const FabObj& phi, const FabObj& rhs) {
   return phi.lay.g >= 2 && rhs.lay.g >= 1 && phi.dtype == rhs.dtype && phi.lay.ncomp == 1;
 }
 
-FusedTable make_fused(Ctx& c, const BoxArray& ba, double h, const FabObj& src, const FabObj& rhs,
-                      const FabObj& dst, const int periodic[3], int ty, cudaStream_t s) {
+// Table of the fused sweep for one configuration: tiles of cfg.ty rows x cfg.zc planes
+// (chunk ends are recomputed by both neighbours), prefetch depth cfg.depth.
+static FusedTable build_fused(Ctx& c, const BoxArray& ba, double h, const FabObj& src,
+                              const FabObj& rhs, const FabObj& dst, const int periodic[3],
+                              FusedCfg cfg, cudaStream_t s) {
   FusedTable t;
-  if (!fused_eligible(src, rhs) || dst.lay.g != src.lay.g || dst.dtype != src.dtype) return t;
-  int maxn1 = 1;
+  int maxn1 = 1, maxn2 = 1;
   for (size_t b = 0; b < ba.boxes.size(); ++b) {
     t.max_pitch = std::max(t.max_pitch, src.lay.pitch[b]);
     t.max_pitch_r = std::max(t.max_pitch_r, rhs.lay.pitch[b]);
     maxn1 = std::max(maxn1, ba.boxes[b].len(1));
+    maxn2 = std::max(maxn2, ba.boxes[b].len(2));
   }
-  t.ty = std::max(1, std::min(ty, maxn1));
-  t.depth = 2;
-  if (fused_smem_bytes(src.dtype, t.ty, t.max_pitch, t.max_pitch_r, 2) > 113 * 1024) t.depth = 1;
-  while (t.ty > 1 && fused_smem_bytes(src.dtype, t.ty, t.max_pitch, t.max_pitch_r, t.depth) > 200 * 1024)
-    t.ty /= 2;
+  t.ty = std::max(1, std::min(cfg.ty, maxn1));
+  t.zc = std::max(1, std::min(cfg.zc, maxn2));
+  t.depth = cfg.depth;
   if (fused_smem_bytes(src.dtype, t.ty, t.max_pitch, t.max_pitch_r, t.depth) > 200 * 1024) return t;
   std::vector<DRow> rows;
   long long nr = 0;
@@ -325,18 +350,83 @@ FusedTable make_fused(Ctx& c, const BoxArray& ba, double h, const FabObj& src, c
     }
     R.pad_ = fl;
   });
-  std::vector<int2> units;
+  std::vector<int4> units;  // {box, y0 | ty << 16, z0, z1}
   for (size_t b = 0; b < ba.boxes.size(); ++b)
-    for (int y0 = 0; y0 < ba.boxes[b].len(1); y0 += t.ty) units.push_back(make_int2((int)b, y0));
+    for (int z0 = 0; z0 < ba.boxes[b].len(2); z0 += t.zc)
+      for (int y0 = 0; y0 < ba.boxes[b].len(1); y0 += t.ty)
+        units.push_back(make_int4((int)b, y0 | (t.ty << 16), z0,
+                                  std::min(z0 + t.zc, ba.boxes[b].len(2))));
   t.rows = upload_table(c, rows, nr, s);
-  t.units = c.upload(units.data(), units.size() * sizeof(int2), s);
+  t.units = c.upload(units.data(), units.size() * sizeof(int4), s);
   t.nunits = (int)units.size();
   t.ok = true;
   return t;
 }
 
+// Autotuned fused table: the first time a (type, box shape, box count, pitches) is seen,
+// every candidate (tile rows, z-chunk, prefetch depth) is timed on the live fabs -- each
+// writes the same result into dst -- and the fastest is kept for that shape (and appended
+// to the file named by GBMG_TUNE_FILE, if set, which later contexts read back).
+FusedTable make_fused(Ctx& c, const BoxArray& ba, double h, const FabObj& src, const FabObj& rhs,
+                      const FabObj& dst, const int periodic[3], cudaStream_t s) {
+  FusedTable none;
+  if (!fused_eligible(src, rhs) || dst.lay.g != src.lay.g || dst.dtype != src.dtype) return none;
+  int mx[3] = {1, 1, 1}, mp = 0, mpr = 0;
+  for (size_t b = 0; b < ba.boxes.size(); ++b) {
+    for (int d = 0; d < 3; ++d) mx[d] = std::max(mx[d], ba.boxes[b].len(d));
+    mp = std::max(mp, src.lay.pitch[b]);
+    mpr = std::max(mpr, rhs.lay.pitch[b]);
+  }
+  char key[160];
+  std::snprintf(key, sizeof key, "dt%d_b%dx%dx%d_n%zu_p%d_%d_g%d_%d", src.dtype, mx[0], mx[1], mx[2],
+                ba.boxes.size(), mp, mpr, src.lay.g, rhs.lay.g);
+  {
+    std::lock_guard<std::mutex> lk(c.tune_mu);
+    c.load_tune_file();
+    auto it = c.tune.find(key);
+    if (it != c.tune.end()) return build_fused(c, ba, h, src, rhs, dst, periodic, it->second, s);
+  }
+  FusedCfg best{16, 16, 2};
+  float best_ms = 1e30f;
+  FusedTable best_t;
+  cudaEvent_t e0, e1;
+  MG_CK(cudaEventCreate(&e0));
+  MG_CK(cudaEventCreate(&e1));
+  for (int depth : {2, 3})
+    for (int ty : {4, 8, 16, 32}) {
+      if (ty > 2 * mx[1] && ty != 4) continue;
+      for (int zc : {8, 16, 32, 64}) {
+        if (zc > 2 * mx[2] && zc != 8) continue;
+        FusedTable t = build_fused(c, ba, h, src, rhs, dst, periodic, FusedCfg{ty, zc, depth}, s);
+        if (!t.ok) continue;
+        launch_fused(c, t, src.dtype, s);  // warm
+        MG_CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < 3; ++r) launch_fused(c, t, src.dtype, s);
+        MG_CK(cudaEventRecord(e1, s));
+        MG_CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        MG_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = FusedCfg{t.ty, t.zc, t.depth};
+          best_t = std::move(t);
+        }
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check_device_error(c);
+  if (!best_t.ok) return none;
+  {
+    std::lock_guard<std::mutex> lk(c.tune_mu);
+    c.tune[key] = best;
+    c.save_tune_entry(key, best);
+  }
+  return best_t;
+}
+
 void launch_fused(Ctx& c, const FusedTable& t, int dt, cudaStream_t s) {
-  MG_CK(launch_rbgs_fused(dt, t.rows.rows(), (const int2*)t.units->p, t.nunits, t.ty, t.depth,
+  MG_CK(launch_rbgs_fused(dt, t.rows.rows(), (const int4*)t.units->p, t.nunits, t.ty, t.depth,
                           t.max_pitch, t.max_pitch_r, (int*)c.d_err->p, s));
 }
 
@@ -349,7 +439,7 @@ const FusedTable& fused_table(Ctx& c, int64_t src_id, FabObj& src, int64_t rhs_i
                 (long long)dst_id, code, h);
   auto it = c.fused_cache.find(key);
   if (it != c.fused_cache.end()) return *it->second;
-  auto t = std::make_shared<FusedTable>(make_fused(c, src.ba->ba, h, src, rhs, dst, per, 16, c.stream));
+  auto t = std::make_shared<FusedTable>(make_fused(c, src.ba->ba, h, src, rhs, dst, per, c.stream));
   MG_CK(cudaStreamSynchronize(c.stream));
   t->owner_fabs = {src_id, rhs_id, dst_id < 0 ? -dst_id : dst_id};
   c.fused_cache[key] = t;

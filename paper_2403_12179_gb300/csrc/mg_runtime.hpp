@@ -116,6 +116,11 @@ struct OpTable {
 
 struct Hierarchy;
 
+// Launch configuration of the fused sweep: tile rows, z-planes per CTA, prefetch depth.
+struct FusedCfg {
+  int ty = 16, zc = 16, depth = 2;
+};
+
 struct Ctx {
   int device = -1;
   cudaStream_t stream = nullptr;   // context stream (solves)
@@ -148,6 +153,12 @@ struct Ctx {
   std::mutex tag_mu;
   std::map<std::string, std::shared_ptr<TagSet>> tag_cache;
   std::mutex bottom_mu;  // guards bottom_cache
+  // fused-sweep autotuning results per box shape
+  std::mutex tune_mu;
+  std::map<std::string, FusedCfg> tune;
+  bool tune_loaded = false;
+  void load_tune_file();
+  void save_tune_entry(const std::string& key, const FusedCfg& cfg);
   // serving
   struct Server;
   std::shared_ptr<Server> server;
@@ -229,12 +240,12 @@ struct FusedTable {
   bool ok = false;
   OpTable rows;
   DevBufP units;
-  int nunits = 0, ty = 16, depth = 2, max_pitch = 0, max_pitch_r = 0;
+  int nunits = 0, ty = 16, zc = 16, depth = 2, max_pitch = 0, max_pitch_r = 0;
   std::vector<int64_t> owner_fabs;  // for cache invalidation
 };
 bool fused_eligible(const FabObj& phi, const FabObj& rhs);
 FusedTable make_fused(Ctx& c, const BoxArray& ba, double h, const FabObj& src, const FabObj& rhs,
-                      const FabObj& dst, const int periodic[3], int ty, cudaStream_t s);
+                      const FabObj& dst, const int periodic[3], cudaStream_t s);
 void launch_fused(Ctx& c, const FusedTable& t, int dt, cudaStream_t s);
 // Cached fused table for (src, rhs, dst, bc, h); src/rhs/dst ids are the fab handles (0 for
 // internal fabs, which must then be cached by their owner instead).

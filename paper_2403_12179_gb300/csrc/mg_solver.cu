@@ -69,8 +69,8 @@ void build_tables(Ctx& c, Hierarchy& H, cudaStream_t s) {
     if (D.fused) {
       int per[3];
       bc_code(&H.bc, per);
-      D.f_ab = make_fused(c, ba, D.h, *D.phi, *D.rhs, *D.phi2, per, 16, s);
-      D.f_ba = make_fused(c, ba, D.h, *D.phi2, *D.rhs, *D.phi, per, 16, s);
+      D.f_ab = make_fused(c, ba, D.h, *D.phi, *D.rhs, *D.phi2, per, s);
+      D.f_ba = make_fused(c, ba, D.h, *D.phi2, *D.rhs, *D.phi, per, s);
       if (!D.f_ab.ok || !D.f_ba.ok) D.fused = false;
     }
     if (l + 1 < nl) {

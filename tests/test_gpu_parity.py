@@ -308,7 +308,8 @@ def test_full_size_dirichlet_256(gctx, orc):
 # ---- fused red + black sweep (TMA-staged z-slabs) ---------------------------------------
 
 FUSED_CASES = [((63, 63, 63), (64, 64, 64)), ((47, 37, 21), (24, 19, 11)), ((15, 15, 15), (4, 4, 4)),
-               ((31, 31, 31), (16, 16, 16)), ((7, 9, 5), (3, 5, 6))]
+               ((31, 31, 31), (16, 16, 16)), ((7, 9, 5), (3, 5, 6)), ((15, 15, 39), (8, 16, 40)),
+               ((19, 7, 47), (20, 8, 33))]
 
 
 @pytest.mark.parametrize("dom,mb", FUSED_CASES)
