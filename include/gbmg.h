@@ -76,6 +76,10 @@ typedef struct {
   int use_graph;      /* 1 (default): replay each V-cycle as a CUDA graph */
   int fixed_vcycles;  /* >= 0: run exactly this many V-cycles, no stop test; -1 default */
   double h;           /* cell size; 0 (default) means 1 / (domain x extent) */
+  int coarse_cells;   /* the levels from the first one with at most this many cells down to
+                         the bottom run as ONE launch per V-cycle (one CTA per solve, levels
+                         held in shared memory; same arithmetic, bit-identical results).
+                         0 (default): 512 for FP64 levels, 4096 for FP32 levels; -1: off */
 } mg_options;
 
 typedef struct {

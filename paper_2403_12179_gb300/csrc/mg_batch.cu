@@ -110,16 +110,28 @@ struct JobB {
   }
 };
 
+struct CoarseB {
+  std::vector<CoarseJob> v;
+  size_t smem = 0;
+  size_t off = 0;
+  void add(const Hierarchy& H) {
+    v.push_back(H.cjob_host);
+    smem = std::max(smem, H.csmem);
+  }
+};
+
 struct LevelLists {
   SegB half, half_all, rr, prolong;
   TagB fill1_half, fill1_all, fill2_phi, fill2_phi2, fill_rhs;
   UnitB fab, fba;
-  JobB bottom_next;  // bottoms at level l + 1
+  JobB bottom_next;      // bottoms at level l + 1
+  CoarseB coarse_next;   // coarse cycles from level l + 1
 };
 
 struct StepLists {
   std::vector<LevelLists> L;
   JobB bottom0;
+  CoarseB coarse0;
   SegB resid0, rhsabs0, scale0, correct0, zero0;
   TagB fill_phi0;
   int dt = DT_F64;
@@ -177,7 +189,8 @@ void build_lists(Ctx& c, StepLists& S, const std::vector<Member*>& run,
     S.nu2 = H.p.nu2;
     const int nl = (int)H.L.size();
     if (nl == 1) S.bottom0.add(H);
-    for (int l = 0; l + 1 < nl; ++l) {
+    if (H.lc == 0 && nl > 1) S.coarse0.add(H);
+    for (int l = 0; l + 1 < nl && l < H.lc; ++l) {
       LevelData& D = H.L[l];
       LevelLists& LL = S.L[l];
       if (D.fused) {
@@ -194,7 +207,8 @@ void build_lists(Ctx& c, StepLists& S, const std::vector<Member*>& run,
       LL.half_all.add(D.smooth, m->slot);
       LL.rr.add(D.rr, m->slot);
       LL.prolong.add(D.prolong, m->slot);
-      if (l + 2 == nl) LL.bottom_next.add(H);
+      if (l + 1 == H.lc) LL.coarse_next.add(H);
+      else if (l + 2 == nl) LL.bottom_next.add(H);
     }
     if (H.mixed) {
       S.scale0.add(H.scale0, m->slot);
@@ -215,13 +229,16 @@ void upload_lists(Ctx& c, StepLists& S, Staging& st, cudaStream_t s) {
   auto tag = [&](TagB& b) { b.off = st.push(b.v); };
   auto unit = [&](UnitB& b) { b.off = st.push(b.v); };
   auto job = [&](JobB& b) { b.off = st.push(b.v); };
+  auto cjob = [&](CoarseB& b) { b.off = st.push(b.v); };
   for (LevelLists& LL : S.L) {
     seg(LL.half); seg(LL.half_all); seg(LL.rr); seg(LL.prolong);
     tag(LL.fill1_half); tag(LL.fill1_all); tag(LL.fill2_phi); tag(LL.fill2_phi2); tag(LL.fill_rhs);
     unit(LL.fab); unit(LL.fba);
     job(LL.bottom_next);
+    cjob(LL.coarse_next);
   }
   job(S.bottom0);
+  cjob(S.coarse0);
   seg(S.resid0); seg(S.rhsabs0); seg(S.scale0); seg(S.correct0); seg(S.zero0);
   tag(S.fill_phi0);
   size_t need = std::max<size_t>(st.host.size(), 256);
@@ -277,6 +294,9 @@ void enqueue_step(Ctx& c, StepLists& S, const unsigned char* dev, unsigned long 
   if (!S.bottom0.v.empty())
     MG_CK(launch_bottom(S.dt, (const BottomJob*)(dev + S.bottom0.off), (int)S.bottom0.v.size(),
                         S.bottom0.maxN, s));
+  if (!S.coarse0.v.empty())
+    MG_CK(launch_coarse_cycle(S.dt, (const CoarseJob*)(dev + S.coarse0.off),
+                              (int)S.coarse0.v.size(), S.coarse0.smem, s));
   for (int l = 0; l < nlev; ++l) {
     LevelLists& LL = S.L[l];
     if (!LL.rr.total) continue;
@@ -287,6 +307,9 @@ void enqueue_step(Ctx& c, StepLists& S, const unsigned char* dev, unsigned long 
     if (!LL.bottom_next.v.empty())
       MG_CK(launch_bottom(S.dt, (const BottomJob*)(dev + LL.bottom_next.off),
                           (int)LL.bottom_next.v.size(), LL.bottom_next.maxN, s));
+    if (!LL.coarse_next.v.empty())
+      MG_CK(launch_coarse_cycle(S.dt, (const CoarseJob*)(dev + LL.coarse_next.off),
+                                (int)LL.coarse_next.v.size(), LL.coarse_next.smem, s));
   }
   for (int l = nlev - 1; l >= 0; --l) {
     LevelLists& LL = S.L[l];

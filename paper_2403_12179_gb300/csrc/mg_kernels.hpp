@@ -65,8 +65,8 @@ struct BottomJob {
 
 // The coarse end of a V-cycle (levels lc .. bottom) in one CTA: every level held densely in
 // shared memory (phi with one ghost layer, then rhs, x fastest), offsets in elements of the
-// level's type.  rows / nbox: level lc's box table (v[0] = phi, v[1] = rhs), through which
-// phi and rhs of level lc are gathered and phi is scattered back.
+// level's type.  Level lc's cell i (dense, x fastest) lives at phi[off_phi[i]] and
+// rhs[off_rhs[i]] in its fabs: phi and rhs are gathered from there and phi scattered back.
 constexpr int kMaxCoarseLevels = 8;
 struct CoarseLevel {
   int n[3];   // level domain extents
@@ -75,9 +75,12 @@ struct CoarseLevel {
   double h2, ih2;
 };
 struct CoarseJob {
-  const DRow* rows;
+  const long long* off_phi;
+  const long long* off_rhs;
+  void* phi;
+  const void* rhs;
   const double* Mt;  // bottom (pseudo-)inverse, transposed, over the last level's cells
-  int nbox, nlev, nu1, nu2, N;
+  int nlev, nu1, nu2, N;
   int periodic[3];
   CoarseLevel lev[kMaxCoarseLevels];
 };
@@ -184,6 +187,8 @@ cudaError_t launch_bottom(int dt, const BottomJob* jobs, int njobs, int maxN, cu
 // value over the jobs.
 size_t coarse_smem_bytes(int dt, const int (*n)[3], int nlev);
 constexpr size_t kCoarseSmemMax = 200 * 1024;
+// Raises the kernel's shared-memory limit to smem (once; call outside stream capture).
+cudaError_t coarse_opt_in(int dt, size_t smem);
 cudaError_t launch_coarse_cycle(int dt, const CoarseJob* jobs, int njobs, size_t smem,
                                 cudaStream_t s);
 

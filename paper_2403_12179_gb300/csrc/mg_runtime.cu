@@ -482,6 +482,7 @@ SolveParams params_from(const mg_options* o, const BoxArray& ba) {
     p.use_graph = o->use_graph;
     p.fixed_vcycles = o->fixed_vcycles;
     p.h = o->h;
+    p.coarse_cells = o->coarse_cells;
   }
   if (p.h <= 0.0) p.h = 1.0 / ba.dom.len(0);
   if (p.nu1 < 0 || p.nu2 < 0 || p.max_iter < 0 || p.nu1 + p.nu2 == 0)

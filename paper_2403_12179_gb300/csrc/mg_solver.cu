@@ -140,6 +140,67 @@ void build_tables(Ctx& c, Hierarchy& H, cudaStream_t s) {
   J.N = (int)N;
   H.job = c.upload(&J, sizeof J, s);
   H.job_host = J;
+  // The coarse end of the cycle as one launch: from the first level with at most
+  // `limit` cells whose levels (down to the bottom) fit into shared memory.
+  H.lc = nl;
+  const int limit = H.p.coarse_cells != 0 ? H.p.coarse_cells : (H.dt == DT_F64 ? 512 : 4096);
+  for (int l = std::max(0, nl - kMaxCoarseLevels); H.p.coarse_cells >= 0 && l + 1 < nl; ++l) {
+    if (H.L[l].bao->ba.dom.npts() > limit) continue;
+    int ext[kMaxCoarseLevels][3];
+    for (int k = l; k < nl; ++k)
+      for (int d = 0; d < 3; ++d) ext[k - l][d] = H.L[k].bao->ba.dom.len(d);
+    const size_t smem = coarse_smem_bytes(H.dt, ext, nl - l);
+    if (smem > kCoarseSmemMax) continue;
+    // level l's cells, dense and x fastest, in its phi and rhs fabs
+    const LevelData& T = H.L[l];
+    const BoxArray& tb = T.bao->ba;
+    const long long nt = tb.dom.npts();
+    std::vector<long long> offs(2 * nt);
+    for (size_t b = 0; b < tb.boxes.size(); ++b) {
+      const Box& X = tb.boxes[b];
+      for (int z = X.lo[2]; z <= X.hi[2]; ++z)
+        for (int y = X.lo[1]; y <= X.hi[1]; ++y)
+          for (int x = X.lo[0]; x <= X.hi[0]; ++x) {
+            long long i = ((long long)(z - tb.dom.lo[2]) * ext[0][1] + (y - tb.dom.lo[1])) *
+                              ext[0][0] + (x - tb.dom.lo[0]);
+            offs[i] = T.phi->lay.at(tb, (int)b, x, y, z);
+            offs[nt + i] = T.rhs->lay.at(tb, (int)b, x, y, z);
+          }
+    }
+    H.coff = c.upload(offs.data(), offs.size() * 8, s);
+    CoarseJob& C = H.cjob_host;
+    C = CoarseJob{};
+    C.off_phi = (const long long*)H.coff->p;
+    C.off_rhs = C.off_phi + nt;
+    C.phi = T.phi->base;
+    C.rhs = T.rhs->base;
+    C.Mt = J.Mt;
+    C.N = J.N;
+    C.nlev = nl - l;
+    C.nu1 = H.p.nu1;
+    C.nu2 = H.p.nu2;
+    for (int d = 0; d < 3; ++d) C.periodic[d] = per[d];
+    int off = 0;
+    for (int k = 0; k < C.nlev; ++k) {
+      const LevelData& D = H.L[l + k];
+      CoarseLevel& V = C.lev[k];
+      for (int d = 0; d < 3; ++d) {
+        V.n[d] = ext[k][d];
+        V.lo[d] = D.bao->ba.dom.lo[d];
+      }
+      V.h2 = D.h * D.h;
+      V.ih2 = 1.0 / (D.h * D.h);
+      V.off_phi = off;
+      off += (V.n[0] + 2) * (V.n[1] + 2) * (V.n[2] + 2);
+      V.off_rhs = off;
+      off += V.n[0] * V.n[1] * V.n[2];
+    }
+    H.csmem = smem;
+    MG_CK(coarse_opt_in(H.dt, smem));
+    H.cjob = c.upload(&C, sizeof C, s);
+    H.lc = l;
+    break;
+  }
   // fill plans must exist before any graph capture
   for (auto& D : H.L) {
     fill_plan(c, *D.phi, &H.bc, 1);
@@ -161,7 +222,8 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
   for (auto& h : c.hier) {
     if (h->rhs_id == rhs.id && h->phi_id == phi.id && h->bc_key == key &&
         h->p.nu1 == p.nu1 && h->p.nu2 == p.nu2 && h->p.precision == p.precision &&
-        h->p.smoother == p.smoother && h->p.h == p.h)
+        h->p.smoother == p.smoother && h->p.h == p.h &&
+        h->p.coarse_cells == p.coarse_cells)
       return *h;
   }
   if (rhs.dtype != DT_F64 || phi.dtype != DT_F64) fail(MG_EINVAL, "mg_solve needs FP64 fabs");
@@ -242,15 +304,17 @@ void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s) {
 
 void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s) {
   const int nl = (int)H.L.size();
-  for (int l = 0; l + 1 < nl; ++l) {
+  const int top = H.lc < nl ? H.lc : nl - 1;  // levels below `top` run stage by stage
+  for (int l = 0; l < top; ++l) {
     LevelData& D = H.L[l];
     if (D.fused) launch_fill(c, *D.rhs, &H.bc, s);  // rhs ghosts for the redundant ring
     smooth(c, H, D, H.p.nu1, s);
     launch_fill(c, *D.phi, &H.bc, s, 1);
     MG_CK(launch_residual_restrict(H.dt, D.rr.rows(), D.rr.nbox, D.rr.nrows, s));
   }
-  MG_CK(launch_bottom(H.dt, (const BottomJob*)H.job->p, 1, H.N, s));
-  for (int l = nl - 2; l >= 0; --l) {
+  if (H.lc < nl) MG_CK(launch_coarse_cycle(H.dt, (const CoarseJob*)H.cjob->p, 1, H.csmem, s));
+  else MG_CK(launch_bottom(H.dt, (const BottomJob*)H.job->p, 1, H.N, s));
+  for (int l = top - 1; l >= 0; --l) {
     LevelData& D = H.L[l];
     MG_CK(launch_prolong_add(H.dt, D.prolong.rows(), D.prolong.nbox, D.prolong.nrows, s));
     smooth(c, H, D, H.p.nu2, s);

@@ -30,6 +30,11 @@ struct Hierarchy {
   OpTable resid0, rhsabs0, scale0, correct0, zero0_64;
   DevBufP Mt, offr, offp, job;
   int N = 0;
+  // levels [lc, L.size()) run as one coarse-cycle launch; lc == L.size(): not used
+  int lc = 0;
+  size_t csmem = 0;
+  DevBufP cjob, coff;
+  CoarseJob cjob_host{};
   DevBufP dnorm;  // [0] residual norm bits, [1] rhs norm bits
   unsigned long long* hnorm = nullptr;
   BottomJob job_host{};

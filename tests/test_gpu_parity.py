@@ -355,3 +355,61 @@ def test_fused_solver_equals_half_sweep_solver(gctx, orc, periodic):
         out.append((gu.fab_dense(gctx, fp, rhs.shape), res.vcycles, res.status))
     assert out[0][2] == out[1][2] == mg.MG_OK and out[0][1] == out[1][1]
     assert np.array_equal(out[0][0], out[1][0])
+
+
+# ---- the coarse end of the cycle as one launch -----------------------------------------
+
+COARSE_CASES = [
+    # domain extents, max box, periodic, precision, coarse_cells
+    ((32, 32, 32), (16, 16, 16), (1, 1, 1), mg.MG_PREC_F64, 0),
+    ((32, 32, 32), (8, 8, 8), (0, 0, 0), mg.MG_PREC_F64, 4096),
+    ((64, 32, 16), (16, 16, 16), (1, 0, 1), mg.MG_PREC_F64, 0),
+    ((24, 24, 24), (8, 8, 8), (0, 1, 0), mg.MG_PREC_MIXED, 0),
+    ((48, 48, 48), (16, 16, 16), (0, 0, 0), mg.MG_PREC_MIXED, 0),
+    ((16, 16, 16), (8, 8, 8), (0, 0, 0), mg.MG_PREC_F64, 4096),    # whole cycle in one launch
+    ((16, 16, 16), (16, 16, 16), (1, 1, 1), mg.MG_PREC_MIXED, 0),  # ... in mixed precision
+]
+
+
+def _solve_with(gctx, ext, mb, periodic, rhs, phi0, opt):
+    dom = tuple(e - 1 for e in ext)
+    ba, _ = _ba(gctx, dom, mb)
+    fr = gu.dense_fab(gctx, ba, rhs, 0)
+    fp = gu.dense_fab(gctx, ba, phi0, 1)
+    before = mg.mg_kernel_launches()
+    res = mg.mg_solve(gctx, fr, fp, mg.make_bc(periodic), 1e-10, opt)
+    launches = mg.mg_kernel_launches() - before
+    phi = gu.fab_dense(gctx, fp, rhs.shape)
+    mg.mg_fab_free(gctx, fr)
+    mg.mg_fab_free(gctx, fp)
+    return phi, res, launches
+
+
+@pytest.mark.parametrize("ext,mb,periodic,precision,cells", COARSE_CASES)
+def test_coarse_cycle_kernel_bitwise(gctx, orc, ext, mb, periodic, precision, cells):
+    """The one-launch coarse cycle gives bit for bit the iterates of the stage-by-stage cycle
+    (with a non-zero initial guess, which the whole-cycle cases read), in fewer launches."""
+    g = inputs.rng(47)
+    shape = tuple(reversed(ext))
+    rhs = g.standard_normal(shape)
+    if all(periodic):
+        rhs = inputs.remove_mean(rhs)
+    phi0 = 0.1 * g.standard_normal(shape)
+    out = []
+    for c in (cells, -1):
+        opt = mg.make_options(precision=precision, coarse_cells=c)
+        out.append(_solve_with(gctx, ext, mb, periodic, rhs, phi0, opt))
+    (a, ra, la), (b, rb, lb) = out
+    assert ra.status == rb.status == mg.MG_OK
+    assert ra.vcycles == rb.vcycles and ra.rel_resid == rb.rel_resid
+    assert np.array_equal(a, b)
+    assert la < lb
+    # and against the oracle on a fixed number of cycles (FP64 path)
+    if precision == mg.MG_PREC_F64:
+        opt = mg.make_options(coarse_cells=cells, fixed_vcycles=2)
+        c, _, _ = _solve_with(gctx, ext, mb, periodic, rhs, np.zeros(shape), opt)
+        dom = tuple(e - 1 for e in ext)
+        o_phi, _, vc, _ = orc.solve(Z3, dom, periodic, orc.chop(Z3, dom, mb), 1.0 / ext[0], rhs,
+                                    fixed_vcycles=2)
+        assert vc == 2
+        assert np.abs(c - o_phi).max() <= 1e-12 * np.abs(o_phi).max()
