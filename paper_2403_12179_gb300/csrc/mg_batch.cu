@@ -196,9 +196,9 @@ void build_lists(Ctx& c, StepLists& S, const std::vector<Member*>& run,
       if (D.fused) {
         LL.fab.add(D.f_ab);
         LL.fba.add(D.f_ba);
-        LL.fill2_phi.add(fill_plan(c, *D.phi, &H.bc), D.phi->base);
-        LL.fill2_phi2.add(fill_plan(c, *D.phi2, &H.bc), D.phi2->base);
-        LL.fill_rhs.add(fill_plan(c, *D.rhs, &H.bc), D.rhs->base);
+        LL.fill2_phi.add(fill_plan(c, *D.phi, &H.bc, 2), D.phi->base);
+        LL.fill2_phi2.add(fill_plan(c, *D.phi2, &H.bc, 2), D.phi2->base);
+        LL.fill_rhs.add(fill_plan(c, *D.rhs, &H.bc, 1), D.rhs->base);
       } else {
         LL.half.add(D.smooth, m->slot);
         LL.fill1_half.add(fill_plan(c, *D.phi, &H.bc, 1), D.phi->base);

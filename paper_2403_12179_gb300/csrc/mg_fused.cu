@@ -278,114 +278,90 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsi
       }
     }
 
+    // Stage s red-updates plane s and black-updates plane s-1.  Both passes map (row, x) to
+    // the same thread, and the red cell (x, y, s) sits right above the black cell
+    // (x, y, s-1): the red update reads that black cell's old value, the black update reads
+    // the red cell's new one, and every other input of either update was finished in an
+    // earlier stage.  So the two passes need no barrier between them.
     T* P0 = pbuf + (size_t)pslot(s - 1) * phi_buf_elems;
     T* P1 = pbuf + (size_t)pslot(s) * phi_buf_elems;
-    T* P2 = pbuf + (size_t)pslot(s + 1) * phi_buf_elems;
+    const T* P2 = pbuf + (size_t)pslot(s + 1) * phi_buf_elems;
     const T* Q = rbuf + (size_t)rslot(s) * rhs_buf_elems;
     // element (x, y) of a phi buffer: [(y - y0 + 2) * pitch + x + g]; rhs: [(y - y0 + 1) * pr + x + gr]
     const int gz = S.loz + s;
-    // ---- red half of plane s
+    // red rows [ya, yb] of plane s: planes outside [z0, z1) are needed only under the tile
+    // (as z-neighbours of black cells), the others with a one-row ring
+    const bool ghost_plane = (s < z0 || s >= z1);
+    const bool red = !((s < 0 && (S.flags & 4)) || (s >= nzl && (S.flags & 32)));
+    int ya = ghost_plane ? S.y0 : S.y0 - 1;
+    int yb = ghost_plane ? S.y0 + S.ty - 1 : S.y0 + S.ty;
+    if (!ghost_plane) {
+      if (ya < 0 && (S.flags & 2)) ya = 0;
+      if (yb >= S.ny && (S.flags & 16)) yb = S.ny - 1;
+    }
+    const bool black = (s - 1 >= z0 && s - 1 < z1);  // black rows [y0, y0+ty) of plane s-1
+    const T* B0 = black ? pbuf + (size_t)pslot(s - 2) * phi_buf_elems : P0;
+    const T* QB = black ? rbuf + (size_t)rslot(s - 1) * rhs_buf_elems : Q;
     {
-      // planes outside [z0, z1) are needed only under the tile (z-neighbours of black cells)
-      const bool ghost_plane = (s < z0 || s >= z1);
-      const bool skip = (s < 0 && (S.flags & 4)) || (s >= nzl && (S.flags & 32));
-      if (!skip) {
-        int ya = ghost_plane ? S.y0 : S.y0 - 1;
-        int yb = ghost_plane ? S.y0 + S.ty - 1 : S.y0 + S.ty;
-        if (!ghost_plane) {
-          if (ya < 0 && (S.flags & 2)) ya = 0;
-          if (yb >= S.ny && (S.flags & 16)) yb = S.ny - 1;
-        }
-        // cells 0 <= x < nx of rows ya..yb: lanes cover (row, x-pair); pointers advance by
-        // whole rows, the red parity flips with each odd row step
-        int y = ya + row0;
-        if (y <= yb) {
-          const T* p0 = P0 + (y - S.y0 + 2) * S.pitch + S.g;
-          T* p1 = P1 + (y - S.y0 + 2) * S.pitch + S.g;
-          const T* p2 = P2 + (y - S.y0 + 2) * S.pitch + S.g;
-          const T* q = Q + (y - S.y0 + 1) * S.pr + S.gr;
-          int par = (S.lox + S.loy + y + gz) & 1;  // first red x >= 0 in row y
-          const int dstep = row_step * S.pitch, qstep = row_step * S.pr, pflip = row_step & 1;
-          for (; y <= yb; y += row_step) {
-            for (int x = par + 2 * plane_lane; x < S.nx; x += 2 * lpr) {
-              T* c = p1 + x;
-              T a = c[-1];
-              a = Ar<T>::add(a, c[1]);
-              a = Ar<T>::add(a, c[-S.pitch]);
-              a = Ar<T>::add(a, c[S.pitch]);
-              a = Ar<T>::add(a, p0[x]);
-              a = Ar<T>::add(a, p2[x]);
-              *c = gs_update(a, q[x], S.mh2);
-            }
-            p0 += dstep;
-            p1 += dstep;
-            p2 += dstep;
-            q += qstep;
-            par ^= pflip;
+      int y = S.y0 - 1 + row0;
+      int par = (S.lox + S.loy + y + gz) & 1;  // first red x >= 0 of row y in plane s
+      const int pflip = row_step & 1;
+      for (; y <= S.y0 + S.ty; y += row_step, par ^= pflip) {
+        const bool r_on = red && y >= ya && y <= yb;
+        const bool b_on = black && y >= S.y0 && y < S.y0 + S.ty;
+        if (!r_on && !b_on) continue;
+        const int o = (y - S.y0 + 2) * S.pitch + S.g;
+        const int oq = (y - S.y0 + 1) * S.pr + S.gr;
+        T* p1 = P1 + o;
+        T* p0 = P0 + o;
+        for (int x = par + 2 * plane_lane; x < S.nx; x += 2 * lpr) {
+          T zr = p1[x];  // red value above the black cell: new if updated now
+          if (r_on) {
+            T a = p1[x - 1];
+            a = Ar<T>::add(a, p1[x + 1]);
+            a = Ar<T>::add(a, p1[x - S.pitch]);
+            a = Ar<T>::add(a, p1[x + S.pitch]);
+            a = Ar<T>::add(a, p0[x]);
+            a = Ar<T>::add(a, P2[o + x]);
+            zr = gs_update(a, Q[oq + x], S.mh2);
+            p1[x] = zr;
           }
-        }
-        // ring cells x = -1 and x = nx of rows inside the box (their red value feeds the
-        // black update of x = 0 / nx-1), one thread per row
-        if (!ghost_plane) {
-          const bool lo_in = !(S.flags & 1), hi_in = !(S.flags & 8);
-          for (int y = ya + tid; y <= yb; y += blockDim.x) {
-            if (y < 0 || y >= S.ny) continue;
-            const int gy = S.loy + y;
-            const int orow = (y - S.y0 + 2) * S.pitch + S.g;
-            const int qrow = (y - S.y0 + 1) * S.pr + S.gr;
-            for (int side = 0; side < 2; ++side) {
-              const int x = side ? S.nx : -1;
-              if (!(side ? hi_in : lo_in) || ((S.lox + x + gy + gz) & 1)) continue;
-              const int o = orow + x;
-              T a = P1[o - 1];
-              a = Ar<T>::add(a, P1[o + 1]);
-              a = Ar<T>::add(a, P1[o - S.pitch]);
-              a = Ar<T>::add(a, P1[o + S.pitch]);
-              a = Ar<T>::add(a, P0[o]);
-              a = Ar<T>::add(a, P2[o]);
-              P1[o] = gs_update(a, Q[qrow + x], S.mh2);
-            }
+          if (b_on) {
+            T a = p0[x - 1];
+            a = Ar<T>::add(a, p0[x + 1]);
+            a = Ar<T>::add(a, p0[x - S.pitch]);
+            a = Ar<T>::add(a, p0[x + S.pitch]);
+            a = Ar<T>::add(a, B0[o + x]);
+            a = Ar<T>::add(a, zr);
+            p0[x] = gs_update(a, QB[oq + x], S.mh2);
           }
         }
       }
     }
-    __syncthreads();
-    // ---- black half of plane s-1 (tile cells only); stored at the start of stage s+1
-    const int pb = s - 1;
-    if (pb >= z0 && pb < z1) {
-      T* B0 = pbuf + (size_t)pslot(pb - 1) * phi_buf_elems;
-      T* B1 = P0;
-      T* B2 = P1;
-      const T* QB = rbuf + (size_t)rslot(pb) * rhs_buf_elems;
-      const int gzb = S.loz + pb;
-      int y = S.y0 + row0;
-      if (y < S.y0 + S.ty) {
-        const T* b0 = B0 + (y - S.y0 + 2) * S.pitch + S.g;
-        T* b1 = B1 + (y - S.y0 + 2) * S.pitch + S.g;
-        const T* b2 = B2 + (y - S.y0 + 2) * S.pitch + S.g;
-        const T* q = QB + (y - S.y0 + 1) * S.pr + S.gr;
-        int par = (S.lox + S.loy + y + gzb + 1) & 1;  // first black x >= 0 in row y
-        const int dstep = row_step * S.pitch, qstep = row_step * S.pr, pflip = row_step & 1;
-        for (; y < S.y0 + S.ty; y += row_step) {
-          for (int x = par + 2 * plane_lane; x < S.nx; x += 2 * lpr) {
-            T* c = b1 + x;
-            T a = c[-1];
-            a = Ar<T>::add(a, c[1]);
-            a = Ar<T>::add(a, c[-S.pitch]);
-            a = Ar<T>::add(a, c[S.pitch]);
-            a = Ar<T>::add(a, b0[x]);
-            a = Ar<T>::add(a, b2[x]);
-            *c = gs_update(a, q[x], S.mh2);
-          }
-          b0 += dstep;
-          b1 += dstep;
-          b2 += dstep;
-          q += qstep;
-          par ^= pflip;
+    // red ring cells x = -1 and x = nx of rows inside the box (their red value feeds the
+    // black update of x = 0 / nx-1 in the next stage), one thread per row
+    if (red && !ghost_plane) {
+      const bool lo_in = !(S.flags & 1), hi_in = !(S.flags & 8);
+      for (int y = ya + tid; y <= yb; y += blockDim.x) {
+        if (y < 0 || y >= S.ny) continue;
+        const int gy = S.loy + y;
+        const int orow = (y - S.y0 + 2) * S.pitch + S.g;
+        const int qrow = (y - S.y0 + 1) * S.pr + S.gr;
+        for (int side = 0; side < 2; ++side) {
+          const int x = side ? S.nx : -1;
+          if (!(side ? hi_in : lo_in) || ((S.lox + x + gy + gz) & 1)) continue;
+          const int o = orow + x;
+          T a = P1[o - 1];
+          a = Ar<T>::add(a, P1[o + 1]);
+          a = Ar<T>::add(a, P1[o - S.pitch]);
+          a = Ar<T>::add(a, P1[o + S.pitch]);
+          a = Ar<T>::add(a, P0[o]);
+          a = Ar<T>::add(a, P2[o]);
+          P1[o] = gs_update(a, Q[qrow + x], S.mh2);
         }
       }
-      fence_async_smem();  // make the generic-proxy writes visible to the bulk store
     }
+    fence_async_smem();  // make the generic-proxy writes visible to the bulk stores
   }
   // the last finished plane (z1-1) is stored after the loop
   __syncthreads();

@@ -175,7 +175,7 @@ cudaError_t launch_prolong_add(int dt, const DRow* rows, int nbox, long long nro
 // filled), v[1] = rhs (1 ghost layer, filled), v[2] = destination phi with the source's
 // layout; pad_ = Dirichlet-face flags (bit d: low face of dim d, bit 3+d: high face).
 // units[i] = {box, y0, z0, z1}: rows [y0, y0+ty) x planes [z0, z1) of a box; depth = planes
-// loaded ahead (1 or 2).
+// loaded ahead (1 to 3).
 size_t fused_smem_bytes(int dt, int ty, int max_pitch, int max_pitch_r, int depth);
 cudaError_t launch_rbgs_fused(int dt, const DRow* rows, const int4* units, int nunits, int ty,
                               int depth, int max_pitch, int max_pitch_r, int* err,

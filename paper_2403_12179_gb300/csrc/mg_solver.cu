@@ -205,9 +205,9 @@ void build_tables(Ctx& c, Hierarchy& H, cudaStream_t s) {
   for (auto& D : H.L) {
     fill_plan(c, *D.phi, &H.bc, 1);
     if (D.fused) {
-      fill_plan(c, *D.phi, &H.bc);
-      fill_plan(c, *D.phi2, &H.bc);
-      fill_plan(c, *D.rhs, &H.bc);
+      fill_plan(c, *D.phi, &H.bc, 2);
+      fill_plan(c, *D.phi2, &H.bc, 2);
+      fill_plan(c, *D.rhs, &H.bc, 1);
     }
   }
   fill_plan(c, *H.phi0, &H.bc, 1);
@@ -289,9 +289,9 @@ void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s) {
   if (D.fused) {
     // pairs of fused sweeps: phi -> phi2 -> phi
     for (; k + 1 < sweeps; k += 2) {
-      launch_fill(c, *D.phi, &H.bc, s);
+      launch_fill(c, *D.phi, &H.bc, s, 2);  // the fused sweep reads two layers
       launch_fused(c, D.f_ab, H.dt, s);
-      launch_fill(c, *D.phi2, &H.bc, s);
+      launch_fill(c, *D.phi2, &H.bc, s, 2);
       launch_fused(c, D.f_ba, H.dt, s);
     }
   }
@@ -307,7 +307,7 @@ void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s) {
   const int top = H.lc < nl ? H.lc : nl - 1;  // levels below `top` run stage by stage
   for (int l = 0; l < top; ++l) {
     LevelData& D = H.L[l];
-    if (D.fused) launch_fill(c, *D.rhs, &H.bc, s);  // rhs ghosts for the redundant ring
+    if (D.fused) launch_fill(c, *D.rhs, &H.bc, s, 1);  // rhs ghosts for the redundant ring
     smooth(c, H, D, H.p.nu1, s);
     launch_fill(c, *D.phi, &H.bc, s, 1);
     MG_CK(launch_residual_restrict(H.dt, D.rr.rows(), D.rr.nbox, D.rr.nrows, s));

@@ -75,7 +75,8 @@ def _apply_tags(tags, boxes, fabs, ng):
 @pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (0, 1, 0), (1, 0, 1)])
 @pytest.mark.parametrize("dom,mb,ng", [((11, 9, 7), (5, 4, 8), 2), ((15, 15, 15), (8, 8, 8), 1),
                                        ((3, 3, 3), (4, 4, 4), 2), ((1, 2, 1), (2, 3, 2), 1),
-                                       ((23, 15, 7), (8, 8, 8), 2)])
+                                       ((23, 15, 7), (8, 8, 8), 2), ((11, 9, 7), (5, 4, 8), 4),
+                                       ((15, 15, 15), (4, 4, 4), 4)])
 def test_copy_tags_reproduce_oracle_fill_bitwise(hctx, orc, periodic, dom, mb, ng):
     if not all(periodic) and any(ng > d + 1 for d, p in zip(dom, periodic) if not p):
         pytest.skip("ghost wider than a Dirichlet extent")

@@ -315,26 +315,28 @@ FUSED_CASES = [((63, 63, 63), (64, 64, 64)), ((47, 37, 21), (24, 19, 11)), ((15,
 @pytest.mark.parametrize("dom,mb", FUSED_CASES)
 @pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (1, 0, 0), (0, 1, 1)])
 @pytest.mark.parametrize("dt", [mg.MG_F64, mg.MG_F32])
-def test_fused_sweep_bitwise(gctx, orc, dom, mb, periodic, dt):
+@pytest.mark.parametrize("gp,gr", [(2, 1), (4, 3)])
+def test_fused_sweep_bitwise(gctx, orc, dom, mb, periodic, dt, gp, gr):
+    """Ghost widths: phi 2 / rhs 1 (the minimum) and wider ones (the sweep reads two / one)."""
     npdt = np.float64 if dt == mg.MG_F64 else np.float32
     h = 1.0 / (dom[0] + 1)
     ba, boxes = _ba(gctx, dom, mb)
     g = inputs.rng(45)
-    phi = [g.standard_normal(f.shape).astype(npdt) for f in orc.new_field(boxes, 2)]
-    rhs = [g.standard_normal(f.shape).astype(npdt) for f in orc.new_field(boxes, 1)]
+    phi = [g.standard_normal(f.shape).astype(npdt) for f in orc.new_field(boxes, gp)]
+    rhs = [g.standard_normal(f.shape).astype(npdt) for f in orc.new_field(boxes, gr)]
     ref = phi
     for color in (0, 1):
-        ref = orc.fill_boundary(Z3, dom, periodic, boxes, ref, 2)
-        ref = orc.rbgs(Z3, dom, boxes, h, ref, 2, rhs, 1, color)
+        ref = orc.fill_boundary(Z3, dom, periodic, boxes, ref, gp)
+        ref = orc.rbgs(Z3, dom, boxes, h, ref, gp, rhs, gr, color)
     bc = mg.make_bc(periodic)
-    fa, fr = gu.to_fab(gctx, ba, phi, 2, dt), gu.to_fab(gctx, ba, rhs, 1, dt)
-    fb = mg.mg_fab_alloc(gctx, ba, 1, 2, dt)
+    fa, fr = gu.to_fab(gctx, ba, phi, gp, dt), gu.to_fab(gctx, ba, rhs, gr, dt)
+    fb = mg.mg_fab_alloc(gctx, ba, 1, gp, dt)
     mg.mg_fill_boundary(gctx, fa, bc)
     mg.mg_fill_boundary(gctx, fr, bc)
     mg.mg_smooth_fused(gctx, fa, fr, fb, bc, h)
     got = gu.from_fab(gctx, fb, len(boxes))
     for a, r in zip(got, ref):
-        assert np.array_equal(gu.valid(a, 2), gu.valid(r, 2))
+        assert np.array_equal(gu.valid(a, gp), gu.valid(r, gp))
     for f in (fa, fr, fb):
         mg.mg_fab_free(gctx, f)
 
