@@ -149,8 +149,9 @@ __device__ __forceinline__ T* line(const DView& v, int y, int z) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Copy tags (ghost fill).  One warp per chunk of kTagChunk destination cells of one tag;
-// lanes walk the tag region x fastest.  Segments = fabs.
+// Copy tags (ghost fill).  One warp per chunk of whole x-rows of one tag (tag_chunk_rows).
+// Segments = fabs.  Sources are valid cells and destinations ghost cells, never the same
+// memory within a launch, so sources are read through the read-only path.
 __device__ __forceinline__ int find_tagseg(const TagSeg* __restrict__ segs, int n, long long w) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -161,7 +162,19 @@ __device__ __forceinline__ int find_tagseg(const TagSeg* __restrict__ segs, int 
 }
 
 template <class T>
+__device__ __forceinline__ T tag_value(const T* p, int sign) {
+  if (sign == 0) return T(0);
+  const T v = __ldg(p);
+  return sign > 0 ? v : Ar<T>::neg(v);
+}
+
+// A lane handles cells lane, lane + 32, ... of its warp's chunk (x fastest), U at a time
+// (the chunk's cells per lane): all loads of a batch are issued before its stores, so each
+// lane keeps several independent loads in flight (the fill is bound by memory latency, not
+// bandwidth).  NC = 1: one component; NC = 0: ncomp components.
+template <class T, int NC>
 __global__ void __launch_bounds__(256) k_copy_tags(TagList L, long long nchunks, int ncomp) {
+  constexpr int U = (NC == 1 ? kTagChunk1 : kTagChunkN) / 32;
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (w >= nchunks) return;
   const int lane = threadIdx.x & 31;
@@ -169,22 +182,26 @@ __global__ void __launch_bounds__(256) k_copy_tags(TagList L, long long nchunks,
   if (L.n > 1) S = L.segs[find_tagseg(L.segs, L.n, w)];
   const int2 ch = S.chunks[w - S.chunk_begin];
   const DTag t = S.tags[ch.x];
-  const int ncell = t.ex * t.ey * t.ez;
-  const int end = min(ch.y + kTagChunk, ncell);
+  const int r1 = min(ch.y + tag_chunk_rows(t.ex, ncomp), t.ey * t.ez);
+  const int ncell = (r1 - ch.y) * t.ex;
   T* __restrict__ base = (T*)S.base;
-  for (int l = ch.y + lane; l < end; l += 32) {
-    int x = l % t.ex;
-    int q = l / t.ex;
-    int y = q % t.ey;
-    int z = q / t.ey;
-    long long so = t.src + (long long)x * t.ssx + (long long)y * t.ssy + (long long)z * t.ssz;
-    long long d = t.dst + x + (long long)y * t.dsy + (long long)z * t.dsz;
-    for (int c = 0; c < ncomp; ++c) {
-      T v;
-      if (t.sign == 0) v = T(0);
-      else if (t.sign > 0) v = base[so + c * t.scs];
-      else v = Ar<T>::neg(base[so + c * t.scs]);
-      base[d + c * t.dcs] = v;
+  const int nc = NC ? NC : ncomp;
+  for (int i0 = lane; i0 < ncell; i0 += 32 * U) {
+    long long so[U], d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = min(i0 + 32 * u, ncell - 1);  // tail lanes repeat the last cell
+      const int x = i % t.ex, r = ch.y + i / t.ex;
+      const int y = r % t.ey, z = r / t.ey;
+      so[u] = t.src + (long long)x * t.ssx + (long long)y * t.ssy + (long long)z * t.ssz;
+      d[u] = t.dst + x + (long long)y * t.dsy + (long long)z * t.dsz;
+    }
+    for (int c = 0; c < nc; ++c) {
+      T v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = tag_value(base + so[u] + c * t.scs, t.sign);
+#pragma unroll
+      for (int u = 0; u < U; ++u) base[d[u] + c * t.dcs] = v[u];
     }
   }
 }
@@ -510,7 +527,13 @@ int num_sms() {
 cudaError_t launch_copy_tags_l(int dt, const TagList& L, long long nchunks, int ncomp, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
   unsigned blocks = (unsigned)((nchunks + 7) / 8);
-  GB_DISPATCH(dt, k_copy_tags, blocks, 256, 0, s, L, nchunks, ncomp);
+  if (dt == DT_F64) {
+    if (ncomp == 1) k_copy_tags<double, 1><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
+    else k_copy_tags<double, 0><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
+  } else {
+    if (ncomp == 1) k_copy_tags<float, 1><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
+    else k_copy_tags<float, 0><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
+  }
   count_launches(1);
   return cudaGetLastError();
 }

@@ -85,7 +85,15 @@ struct CoarseJob {
   CoarseLevel lev[kMaxCoarseLevels];
 };
 
-constexpr int kTagChunk = 128;  // destination cells per warp in the copy-tag kernel
+// The copy-tag kernel gives each warp a chunk of whole x-rows of one tag: about kTagChunk1
+// destination cells for one-component fabs, kTagChunkN for more (measured best on GB300),
+// at least one row.  Chunks are int2 {tag, first row}; host and device derive a chunk's row
+// count from the tag's x-extent and the fab's components with tag_chunk_rows.
+constexpr int kTagChunk1 = 64, kTagChunkN = 128;
+__host__ __device__ inline int tag_chunk_rows(int ex, int ncomp) {
+  const int cells = ncomp == 1 ? kTagChunk1 : kTagChunkN;
+  return ex >= cells ? 1 : cells / ex;
+}
 
 // A launch may cover the box tables of several independent solves (batched and served
 // solves): each solve's table is one segment of the launch's row space.  norms and scales

@@ -228,8 +228,8 @@ FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc, int layers) {
     std::vector<DTag> dt = device_tags(ba, f.lay, tags, 0);
     std::vector<int2> chunks;
     for (size_t t = 0; t < dt.size(); ++t) {
-      int n = dt[t].ex * dt[t].ey * dt[t].ez;
-      for (int s0 = 0; s0 < n; s0 += kTagChunk) chunks.push_back(make_int2((int)t, s0));
+      const int rows = dt[t].ey * dt[t].ez, per = tag_chunk_rows(dt[t].ex, f.lay.ncomp);
+      for (int r0 = 0; r0 < rows; r0 += per) chunks.push_back(make_int2((int)t, r0));
     }
     set = std::make_shared<TagSet>();
     set->nchunks = (int)chunks.size();
