@@ -5,7 +5,7 @@ Default workload (dirichlet256): 256^3 homogeneous-Dirichlet FP64 Poisson proble
 64 boxes of 64^3, rhs = seeded N(0,1) smoothed by one damped-Jacobi pass, V(2,2) red-black
 Gauss-Seidel cycles to ||rhs - A phi||_inf <= 1e-10 ||rhs||_inf.  One step = one complete
 solve (phi reset to 0, then mg_solve) with rhs already resident in HBM.  `value` is solves/s
-over all ranks (each rank solves its own replica: the solve does not shard).
+over all ranks (each rank solves its own replica: this solve is not sharded across GPUs).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload dirichlet256|periodic64|mixed512]
