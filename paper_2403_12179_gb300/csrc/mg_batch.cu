@@ -132,7 +132,7 @@ struct StepLists {
   std::vector<LevelLists> L;
   JobB bottom0;
   CoarseB coarse0;
-  SegB resid0, rhsabs0, scale0, correct0, zero0;
+  SegB resid0, rhsabs0, scale0, correct0;
   TagB fill_phi0;
   int dt = DT_F64;
   bool mixed = false;
@@ -213,7 +213,6 @@ void build_lists(Ctx& c, StepLists& S, const std::vector<Member*>& run,
     if (H.mixed) {
       S.scale0.add(H.scale0, m->slot);
       S.correct0.add(H.correct0, m->slot);
-      S.zero0.add(H.L[0].zero, m->slot);
     }
   }
   for (Member* m : check) {
@@ -239,7 +238,7 @@ void upload_lists(Ctx& c, StepLists& S, Staging& st, cudaStream_t s) {
   }
   job(S.bottom0);
   cjob(S.coarse0);
-  seg(S.resid0); seg(S.rhsabs0); seg(S.scale0); seg(S.correct0); seg(S.zero0);
+  seg(S.resid0); seg(S.rhsabs0); seg(S.scale0); seg(S.correct0);
   tag(S.fill_phi0);
   size_t need = std::max<size_t>(st.host.size(), 256);
   if (!st.dev || st.dev->bytes < need) {
@@ -288,8 +287,7 @@ void enqueue_step(Ctx& c, StepLists& S, const unsigned char* dev, unsigned long 
   int* err = (int*)c.d_err->p;
   const int nlev = (int)S.L.size();
   if (S.mixed && S.scale0.total) {
-    MG_CK(launch_residual_scale_f32_l(mk(S.scale0, dev), S.scale0.total, norms, s));
-    MG_CK(launch_set_valid_l(DT_F32, mk(S.zero0, dev), S.zero0.total, 0.0, s));
+    MG_CK(launch_scale_residual_f32_l(mk(S.scale0, dev), S.scale0.total, norms, s));
   }
   if (!S.bottom0.v.empty())
     MG_CK(launch_bottom(S.dt, (const BottomJob*)(dev + S.bottom0.off), (int)S.bottom0.v.size(),

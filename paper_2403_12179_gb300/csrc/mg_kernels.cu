@@ -452,37 +452,50 @@ __device__ __forceinline__ double norm_of(const unsigned long long* norms, int i
 __device__ __forceinline__ double pow2_floor(double s) { return ldexp(1.0, ilogb(s)); }
 __device__ __forceinline__ double pow2_floor_inv(double s) { return ldexp(1.0, -ilogb(s)); }
 
-__global__ void __launch_bounds__(kThreads) k_residual_scale_f32(SegList L, long long nrows,
+// r32 = float(r * 2^-e) with 2^e <= ||r||_inf < 2^(e+1), from the FP64 residual stored by the
+// preceding norm check (the same values the norm was taken over), and the FP32 correction's
+// initial guess e32 = 0.
+__global__ void __launch_bounds__(kThreads) k_scale_residual_f32(SegList L, long long nrows,
                                                                  long long per,
                                                                  const unsigned long long* norms) {
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)(lr % n1), z = (int)(lr / n1);
-    const DView vp = R.v[0];
-    const double* phi = line<double>(vp, y, z);
-    const double* rhs = line<double>(R.v[1], y, z);
-    float* r32 = line<float>(R.c[0], y, z);
-    const double ih2 = R.ih2;
+    const double* __restrict__ r = line<double>(R.v[0], y, z);
+    float* __restrict__ r32 = line<float>(R.c[0], y, z);
+    float* __restrict__ e32 = line<float>(R.c[1], y, z);
     const double down = pow2_floor_inv(norm_of(norms, slot + R.solve));
     for (int x = lane; x < n0; x += 32) {
-      double s = nbr_sum(phi + x, vp.pitch, vp.plane);
-      double v = residual_of(s, phi[x], rhs[x], ih2);
-      r32[x] = __double2float_rn(__dmul_rn(v, down));
+      r32[x] = __double2float_rn(__dmul_rn(__ldg(r + x), down));
+      e32[x] = 0.0f;
     }
   });
 }
 
+// phi += 2^e * e32 (FP64 fma); each lane loads all its cells of a row before storing.
 __global__ void __launch_bounds__(kThreads) k_correct_add(SegList L, long long nrows, long long per,
                                                           const unsigned long long* norms) {
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)(lr % n1), z = (int)(lr / n1);
-    double* phi = line<double>(R.v[0], y, z);
-    const float* e = line<float>(R.c[0], y, z);
+    double* __restrict__ phi = line<double>(R.v[0], y, z);
+    const float* __restrict__ e = line<float>(R.c[0], y, z);
     const double up = pow2_floor(norm_of(norms, slot + R.solve));
-    for (int x = lane; x < n0; x += 32) phi[x] = __fma_rn(up, (double)e[x], phi[x]);
+    int x = lane;
+    for (; x + 96 < n0; x += 128) {
+      double p[4];
+      float v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        p[k] = phi[x + 32 * k];
+        v[k] = __ldg(e + x + 32 * k);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) phi[x + 32 * k] = __fma_rn(up, (double)v[k], p[k]);
+    }
+    for (; x < n0; x += 32) phi[x] = __fma_rn(up, (double)__ldg(e + x), phi[x]);
   });
 }
 
@@ -601,11 +614,11 @@ cudaError_t launch_maxabs_l(int dt, const SegList& L, long long nrows, unsigned 
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual_scale_f32_l(const SegList& L, long long nrows,
+cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,
                                         const unsigned long long* norms, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   Grid g = row_grid(nrows, 16);
-  k_residual_scale_f32<<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
+  k_scale_residual_f32<<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -695,9 +708,9 @@ cudaError_t launch_maxabs(int dt, const DRow* rows, int nbox, long long nrows,
   return launch_maxabs_l(dt, one_seg(rows, nbox), nrows, norms, s);
 }
 
-cudaError_t launch_residual_scale_f32(const DRow* rows, int nbox, long long nrows,
+cudaError_t launch_scale_residual_f32(const DRow* rows, int nbox, long long nrows,
                                       const unsigned long long* norms, cudaStream_t s) {
-  return launch_residual_scale_f32_l(one_seg(rows, nbox), nrows, norms, s);
+  return launch_scale_residual_f32_l(one_seg(rows, nbox), nrows, norms, s);
 }
 
 cudaError_t launch_correct_add(const DRow* rows, int nbox, long long nrows,

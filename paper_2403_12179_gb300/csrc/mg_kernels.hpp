@@ -216,9 +216,10 @@ cudaError_t launch_dense_copy(int dt, const DRow* rows, int nbox, long long nrow
 cudaError_t launch_maxabs(int dt, const DRow* rows, int nbox, long long nrows,
                           unsigned long long* norms, cudaStream_t s);
 
-// Mixed precision.  v[0] = phi (FP64, ghosts filled), v[1] = rhs (FP64), c[0].p = r32 out
-// (FP32, a view with the same box geometry): r32 = float(r / s), s = norms[solve].
-cudaError_t launch_residual_scale_f32(const DRow* rows, int nbox, long long nrows,
+// Mixed precision.  v[0] = r (FP64 residual stored by the norm check), c[0] = r32 out,
+// c[1] = e32 out (FP32 views with the same box geometry): r32 = float(r * 2^-e) with
+// 2^e <= norms[solve] < 2^(e+1), e32 = 0.
+cudaError_t launch_scale_residual_f32(const DRow* rows, int nbox, long long nrows,
                                       const unsigned long long* norms, cudaStream_t s);
 // v[0] = phi (FP64), c[0] = e (FP32 view, same geometry): phi = phi + s * double(e).
 cudaError_t launch_correct_add(const DRow* rows, int nbox, long long nrows,
@@ -235,7 +236,7 @@ cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cuda
 cudaError_t launch_set_valid_l(int dt, const SegList& L, long long nrows, double value, cudaStream_t s);
 cudaError_t launch_maxabs_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
                             cudaStream_t s);
-cudaError_t launch_residual_scale_f32_l(const SegList& L, long long nrows,
+cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,
                                         const unsigned long long* norms, cudaStream_t s);
 cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsigned long long* norms,
                                  cudaStream_t s);

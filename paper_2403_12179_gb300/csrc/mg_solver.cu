@@ -93,14 +93,15 @@ void build_tables(Ctx& c, Hierarchy& H, cudaStream_t s) {
   H.resid0 = make_table(c, ba0, 0, h0, 0, [&](int b, DRow& R) {
     R.v[0] = H.phi0->view(b);
     R.v[1] = H.rhs0->view(b);
+    if (H.mixed) R.v[2] = H.r0->view(b);  // kept for the next outer iteration's scaling
   }, s);
   H.rhsabs0 = make_table(c, ba0, 0, h0, 1, [&](int b, DRow& R) { R.v[0] = H.rhs0->view(b); }, s);
   H.zero0_64 = make_table(c, ba0, 0, h0, 0, [&](int b, DRow& R) { R.v[0] = H.phi0->view(b); }, s);
   if (H.mixed) {
     H.scale0 = make_table(c, ba0, 0, h0, 0, [&](int b, DRow& R) {
-      R.v[0] = H.phi0->view(b);
-      R.v[1] = H.rhs0->view(b);
+      R.v[0] = H.r0->view(b);
       R.c[0] = H.L[0].rhs->view(b);
+      R.c[1] = H.L[0].phi->view(b);
     }, s);
     H.correct0 = make_table(c, ba0, 0, h0, 0, [&](int b, DRow& R) {
       R.v[0] = H.phi0->view(b);
@@ -275,6 +276,7 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
     }
     if (D.fused) D.phi2 = internal_fab(c, D.bao, D.phi->lay.g, H->dt);
   }
+  if (H->mixed) H->r0 = internal_fab(c, phi.ba, 0, DT_F64);
   build_tables(c, *H, s);
   H->dnorm = c.alloc(16, s);
   MG_CK(cudaStreamSynchronize(s));
@@ -325,11 +327,8 @@ void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s) {
 // then the norm check of the new iterate.
 void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
   unsigned long long* dn = (unsigned long long*)H.dnorm->p;
-  if (H.mixed) {
-    MG_CK(launch_residual_scale_f32(H.scale0.rows(), H.scale0.nbox, H.scale0.nrows, dn, s));
-    LevelData& D0 = H.L[0];
-    MG_CK(launch_set_valid(DT_F32, D0.zero.rows(), D0.zero.nbox, D0.zero.nrows, 0.0, s));
-  }
+  if (H.mixed)  // the FP32 right-hand side from the residual of the last norm check; e = 0
+    MG_CK(launch_scale_residual_f32(H.scale0.rows(), H.scale0.nbox, H.scale0.nrows, dn, s));
   enqueue_vcycle(c, H, s);
   if (H.mixed)
     MG_CK(launch_correct_add(H.correct0.rows(), H.correct0.nbox, H.correct0.nrows, dn, s));

@@ -27,6 +27,7 @@ struct Hierarchy {
   bool mixed = false;
   std::vector<LevelData> L;
   std::shared_ptr<FabObj> phi0, rhs0;  // the caller's fabs (FP64)
+  std::shared_ptr<FabObj> r0;          // mixed: FP64 residual stored by each norm check
   OpTable resid0, rhsabs0, scale0, correct0, zero0_64;
   DevBufP Mt, offr, offp, job;
   int N = 0;
