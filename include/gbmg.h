@@ -212,6 +212,10 @@ int mg_fab_set_val(mg_ctx_t ctx, mg_fab_t fab, double v, int include_ghosts, voi
  * Dirichlet face, else (outside the domain across two or more Dirichlet directions) 0. */
 int mg_fill_boundary(mg_ctx_t ctx, mg_fab_t fab, const mg_bc* bc, void* stream);
 
+/* The same ghost fill with one launch per copy tag (Sec. 3.2's unfused form, kept as the
+ * baseline the fused launch is measured against); same results. */
+int mg_fill_boundary_unfused(mg_ctx_t ctx, mg_fab_t fab, const mg_bc* bc, void* stream);
+
 /* Red-black Gauss-Seidel on 1-component fabs of one box array with cell size h.
  * color 0 / 1: one half-sweep of that colour ((i+j+k) mod 2 on global indices), using
  *   phi's ghosts as they are (fill them first); rhs needs no ghosts.

@@ -227,11 +227,15 @@ FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc, int layers) {
     if (!make_copy_tags(ba, per, ng, &tags, &err)) fail(MG_EINVAL, err);
     std::vector<DTag> dt = device_tags(ba, f.lay, tags, 0);
     std::vector<int2> chunks;
+    std::vector<int> first;
     for (size_t t = 0; t < dt.size(); ++t) {
+      first.push_back((int)chunks.size());
       const int rows = dt[t].ey * dt[t].ez, per = tag_chunk_rows(dt[t].ex, f.lay.ncomp);
       for (int r0 = 0; r0 < rows; r0 += per) chunks.push_back(make_int2((int)t, r0));
     }
+    first.push_back((int)chunks.size());
     set = std::make_shared<TagSet>();
+    set->first_chunk = std::move(first);
     set->nchunks = (int)chunks.size();
     if (set->nchunks) {
       set->tags_buf = c.upload(dt.data(), dt.size() * sizeof(DTag), c.stream);
@@ -968,6 +972,22 @@ int mg_fill_boundary(mg_ctx_t h, mg_fab_t fab, const mg_bc* bc, void* stream) {
     if (!c) fail(MG_EINVAL, "ctx is NULL");
     auto f = c->get_fab(fab);
     launch_fill(*c, *f, bc, S(stream));
+    return MG_OK;
+  });
+}
+
+int mg_fill_boundary_unfused(mg_ctx_t h, mg_fab_t fab, const mg_bc* bc, void* stream) {
+  return guard([&] {
+    Ctx* c = (Ctx*)h;
+    if (!c) fail(MG_EINVAL, "ctx is NULL");
+    auto f = c->get_fab(fab);
+    FillPlan& P = fill_plan(*c, *f, bc, -1);
+    cudaStream_t s = S(stream);
+    for (int t = 0; t < P.ntags(); ++t) {
+      const int a = P.set->first_chunk[t], b = P.set->first_chunk[t + 1];
+      if (b > a)
+        MG_CK(launch_copy_tags(f->dtype, P.tags(), P.chunks() + a, b - a, f->base, f->lay.ncomp, s));
+    }
     return MG_OK;
   });
 }

@@ -80,6 +80,7 @@ struct BoxArrayObj {
 struct TagSet {
   DevBufP tags_buf, chunks_buf;
   int nchunks = 0;
+  std::vector<int> first_chunk;  // chunks of tag t: [first_chunk[t], first_chunk[t+1])
 };
 
 // A fab's ghost-fill plan for one set of BCs and number of layers.
@@ -88,6 +89,7 @@ struct FillPlan {
   const DTag* tags() const { return set && set->tags_buf ? (const DTag*)set->tags_buf->p : nullptr; }
   const int2* chunks() const { return set && set->chunks_buf ? (const int2*)set->chunks_buf->p : nullptr; }
   int nchunks() const { return set ? set->nchunks : 0; }
+  int ntags() const { return set ? (int)set->first_chunk.size() - 1 : 0; }
 };
 
 struct FabObj {

@@ -271,6 +271,11 @@ def mg_fill_boundary(ctx, fab, bc, stream=None):
     _ck(lib().mg_fill_boundary(ctx, ctypes.c_int64(fab), ctypes.byref(bc), _s(stream)))
 
 
+def mg_fill_boundary_unfused(ctx, fab, bc, stream=None):
+    """The ghost fill with one launch per copy tag (the unfused baseline)."""
+    _ck(lib().mg_fill_boundary_unfused(ctx, ctypes.c_int64(fab), ctypes.byref(bc), _s(stream)))
+
+
 def mg_smooth(ctx, phi, rhs, bc, h, color, stream=None):
     _ck(lib().mg_smooth(ctx, ctypes.c_int64(phi), ctypes.c_int64(rhs), ctypes.byref(bc),
                         ctypes.c_double(h), ctypes.c_int(color), _s(stream)))

@@ -54,6 +54,22 @@ def test_fill_boundary_bitwise(gctx, orc, dom, mb, ng, ncomp, periodic, dt):
     mg.mg_fab_free(gctx, fab)
 
 
+def test_fill_boundary_unfused_equals_fused(gctx, orc):
+    dom, mb = (23, 15, 7), (8, 8, 8)
+    ba, boxes = _ba(gctx, dom, mb)
+    g = inputs.rng(30)
+    fabs = [g.standard_normal(f.shape) for f in orc.new_field(boxes, 2, 3)]
+    for periodic in [(1, 1, 1), (0, 1, 0)]:
+        bc = mg.make_bc(periodic)
+        a, b = gu.to_fab(gctx, ba, fabs, 2), gu.to_fab(gctx, ba, fabs, 2)
+        mg.mg_fill_boundary(gctx, a, bc)
+        mg.mg_fill_boundary_unfused(gctx, b, bc)
+        for x, y in zip(gu.from_fab(gctx, a, len(boxes)), gu.from_fab(gctx, b, len(boxes))):
+            assert np.array_equal(x, y)
+        mg.mg_fab_free(gctx, a)
+        mg.mg_fab_free(gctx, b)
+
+
 def _level_inputs(orc, boxes, dom, periodic, ng_phi, ng_rhs, seed, dt=np.float64):
     g = inputs.rng(seed)
     phi = [g.standard_normal(f.shape).astype(dt) for f in orc.new_field(boxes, ng_phi)]
