@@ -5,21 +5,22 @@
 // (box, y-tile) and streams its z-planes through shared memory:
 //   * TMA bulk copies (cp.async.bulk, one per plane) bring phi rows [y0-2, y0+TY+2) and rhs
 //     rows [y0-1, y0+TY+1) of each plane into a ring of shared-memory buffers, completing on
-//     mbarriers; loads run D planes ahead of the compute;
-//   * a CTA owns planes [z0, z1) of its tile; stages z0-1 .. z1 each
+//     mbarriers; a producer lane issues each load as soon as its slot is free, D planes
+//     beyond the ones in use;
+//   * a CTA owns planes [z0, z1) of its tile; in stages z0-1 .. z1 the consumer warps
 //     red-update plane s over the tile plus a one-cell ring (the ring cells belong
 //     to neighbouring tiles / boxes / periodic images and are recomputed redundantly from the
 //     second ghost layer -- exactly the values their owners compute; planes z0-1 and z1 are
-//     recomputed the same way under the tile only), then black-updates plane s-1;
-//   * the finished plane s-1 goes back to global memory by one bulk store of whole rows into
-//     the destination buffer (a second phi allocation: tiles read each other's rows as
-//     halos, so the sweep cannot be done in place).
+//     recomputed the same way under the tile only) and black-update plane s-1;
+//   * the producer stores the finished plane s-1 to global memory by one bulk copy of whole
+//     rows into the destination buffer (a second phi allocation: tiles read each other's
+//     rows as halos, so the sweep cannot be done in place).
 // Ghost cells outside the domain (Dirichlet faces) are never updated: a boundary cell's
 // ghost equals -(its own value before this half-sweep), which the fill already holds for
 // every cell that the half-sweep updates.
 //
-// Every mbarrier wait is bounded; on expiry the CTA records an error code, drains its own
-// outstanding copies (again bounded) and returns.
+// Every mbarrier wait is bounded; on expiry the CTA records an error code, the producer
+// drains its outstanding copies (again bounded) and every thread returns.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -131,7 +132,7 @@ struct Sweep {
 
 }  // namespace
 
-// Shared memory: NP phi buffers, NR rhs buffers, then NP + NR mbarriers.
+// Shared memory: NP phi buffers, NR rhs buffers, then NP + NR + kStageBars mbarriers.
 __device__ __forceinline__ int find_unitseg(const UnitSeg* __restrict__ segs, int n, long long u) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -141,9 +142,37 @@ __device__ __forceinline__ int find_unitseg(const UnitSeg* __restrict__ segs, in
   return lo;
 }
 
+// Roles: warps 0..7 (kConsumers threads) update cells; warp 8 lane 0 is the producer, which
+// queues every TMA load as soon as its ring slot is free and stores each finished plane.
+// Consumers wait on the load mbarriers themselves and sync with one named barrier per stage;
+// consumer thread 0 then arrives on the stage's completion mbarrier (stage s on
+// stage_bar[s % kStageBars], so the producer may lag kStageBars - 1 stages without
+// confusing phases).
+constexpr int kConsumers = 256;
+constexpr int kFusedThreads = kConsumers + 32;
+constexpr int kStageBars = 8;
+
+// Named barrier 1 over the consumers; returns the OR of every consumer's flag, the same
+// value in every consumer.
+__device__ __forceinline__ bool consumer_sync_or(bool flag) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)flag), "n"(kConsumers)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsigned phi_buf_elems,
-                                                    unsigned rhs_buf_elems, int* __restrict__ err) {
+__global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty_max,
+                                                              unsigned phi_buf_elems,
+                                                              unsigned rhs_buf_elems,
+                                                              int* __restrict__ err) {
   constexpr int NP = 4 + D;  // live phi planes s-2..s+1 plus D in flight
   constexpr int NR = 2 + D;  // live rhs planes s-1, s plus D in flight
   extern __shared__ __align__(128) unsigned char smem[];
@@ -152,6 +181,7 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsi
   uint64_t* bars = (uint64_t*)(rbuf + (size_t)NR * rhs_buf_elems);
   uint64_t* pbar = bars;
   uint64_t* rbar = bars + NP;
+  uint64_t* sbar = bars + NP + NR;
 
   UnitSeg U = L.one;
   if (L.n > 1) U = L.segs[find_unitseg(L.segs, L.n, blockIdx.x)];
@@ -186,47 +216,80 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsi
 
   if (tid == 0) {
     for (int i = 0; i < NP + NR; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < kStageBars; ++i) mbar_init(&sbar[i], 1);
     fence_mbar_init();
   }
   __syncthreads();
 
-  // global row starts (x = -g) of the first loaded row of plane p
-  auto phi_src = [&](int p) {
-    return src + (long long)p * S.plane + (long long)(S.y0 - 2) * S.pitch - S.g;
-  };
-  auto rhs_src = [&](int p) {
-    return rhs + (long long)p * S.planer + (long long)(S.y0 - 1) * S.pr - S.gr;
-  };
   // planes are loaded in order from z0-2 (phi) / z0-1 (rhs); slot and mbarrier parity
   auto pslot = [&](int p) { return (p - z0 + 2) % NP; };
   auto rslot = [&](int p) { return (p - z0 + 1) % NR; };
   auto pphase = [&](int p) { return (uint32_t)(((p - z0 + 2) / NP) & 1); };
   auto rphase = [&](int p) { return (uint32_t)(((p - z0 + 1) / NR) & 1); };
+  const int s_first = z0 - 1, s_last = z1;  // stages
 
-  const int pmax = z1 + 1;  // last phi plane loaded
-  const int rmax = z1;      // last rhs plane loaded
-  int p_issued = z0 - 3, r_issued = z0 - 2;  // last issued plane
-  auto issue_phi = [&](int p) {
-    if (p > pmax) return;
-    uint64_t* b = &pbar[pslot(p)];
-    mbar_expect_tx(b, S.pbytes);
-    bulk_load(pbuf + (size_t)pslot(p) * phi_buf_elems, phi_src(p), S.pbytes, b);
-    p_issued = p;
-  };
-  auto issue_rhs = [&](int p) {
-    if (p > rmax) return;
-    uint64_t* b = &rbar[rslot(p)];
-    mbar_expect_tx(b, S.rbytes);
-    bulk_load(rbuf + (size_t)rslot(p) * rhs_buf_elems, rhs_src(p), S.rbytes, b);
-    r_issued = p;
-  };
-
-  // Prologue: before stage s, phi planes up to s+D and rhs planes up to s+D-1 are queued.
-  if (tid == 0) {
-    for (int p = z0 - 2; p <= z0 - 1 + D; ++p) issue_phi(p);
-    for (int p = z0 - 1; p <= z0 - 2 + D; ++p) issue_rhs(p);
+  if (tid >= kConsumers) {
+    // ---------------- producer ----------------
+    if (tid != kConsumers) return;
+    const int pmax = z1 + 1, rmax = z1;  // last planes loaded
+    int p_issued = z0 - 3, r_issued = z0 - 2;
+    auto issue_phi = [&](int p) {
+      if (p > pmax) return;
+      uint64_t* b = &pbar[pslot(p)];
+      mbar_expect_tx(b, S.pbytes);
+      bulk_load(pbuf + (size_t)pslot(p) * phi_buf_elems,
+                src + (long long)p * S.plane + (long long)(S.y0 - 2) * S.pitch - S.g, S.pbytes, b);
+      p_issued = p;
+    };
+    auto issue_rhs = [&](int p) {
+      if (p > rmax) return;
+      uint64_t* b = &rbar[rslot(p)];
+      mbar_expect_tx(b, S.rbytes);
+      bulk_load(rbuf + (size_t)rslot(p) * rhs_buf_elems,
+                rhs + (long long)p * S.planer + (long long)(S.y0 - 1) * S.pr - S.gr, S.rbytes, b);
+      r_issued = p;
+    };
+    // every slot starts free
+    for (int p = z0 - 2; p < z0 - 2 + NP; ++p) issue_phi(p);
+    for (int p = z0 - 1; p < z0 - 1 + NR; ++p) issue_rhs(p);
+    bool ok = true;
+    for (int st = s_first; st <= s_last && ok; ++st) {
+      const int k = st - s_first;
+      if (!mbar_wait_bounded(&sbar[k % kStageBars], (uint32_t)((k / kStageBars) & 1))) {
+        ok = false;
+        break;
+      }
+      if (st - 1 >= z0 && st - 1 < z1) {
+        // plane st-1 is final: whole rows y0..y0+ty-1 (the destination's x ghosts are
+        // overwritten; they are refilled before they are read)
+        T* gdst = dst + (long long)(st - 1) * S.plane + (long long)S.y0 * S.pitch - S.g;
+        bulk_store(gdst, pbuf + (size_t)pslot(st - 1) * phi_buf_elems + 2 * S.pitch,
+                   (uint32_t)(S.ty * S.pitch * sizeof(T)));
+        bulk_commit();
+      }
+      // from stage z0 on, phi plane st-2 and rhs plane st-1 (loaded by the prologue or an
+      // earlier stage) were last read in stage st; the store of plane st-2 (issued one
+      // stage earlier) must have finished reading its slot
+      if (st >= z0) {
+        bulk_wait_read1();
+        issue_phi(st - 2 + NP);
+        issue_rhs(st - 1 + NR);
+      }
+    }
+    if (!ok) atomicExch(err, 1);  // the consumers time out on their own
+    // drain: every issued load has landed (consumed or not) and every store has read and
+    // written its data before the CTA's shared memory goes away.  A slot is reissued only
+    // after its previous plane landed and was consumed, so only the latest plane of each
+    // slot can still be in flight (earlier phases of a slot cannot be waited on again).
+    for (int p = max(z0 - 2, p_issued - NP + 1); p <= p_issued; ++p)
+      mbar_wait_bounded(&pbar[pslot(p)], pphase(p));
+    for (int p = max(z0 - 1, r_issued - NR + 1); p <= r_issued; ++p)
+      mbar_wait_bounded(&rbar[rslot(p)], rphase(p));
+    bulk_wait_all();
+    return;
   }
 
+  // ---------------- consumers ----------------
   // Lane mapping of a plane: lanes per row lpr = smallest power of two >= the row's
   // x-pairs (at most 32); a warp covers 32 / lpr rows per pass, the 8 warps interleave.
   const int npv = (S.nx + 1) >> 1;
@@ -235,49 +298,16 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsi
   const int lpr = 1 << lsh;
   const int plane_lane = (tid & 31) & (lpr - 1);
   const int row0 = (tid >> 5) * (32 >> lsh) + ((tid & 31) >> lsh);
-  const int row_step = (blockDim.x >> 5) * (32 >> lsh);
+  const int row_step = (kConsumers >> 5) * (32 >> lsh);
 
-  __shared__ int s_ok;
-  bool ok = true;
-  int p_done = z0 - 3, r_done = z0 - 2;  // planes thread 0 has seen land
-  auto store_plane = [&](int pb) {
-    // whole rows y0..y0+ty-1 of plane pb (x ghosts of the destination get overwritten;
-    // they are refilled before they are read)
-    T* gdst = dst + (long long)pb * S.plane + (long long)S.y0 * S.pitch - S.g;
-    bulk_store(gdst, pbuf + (size_t)pslot(pb) * phi_buf_elems + 2 * S.pitch,
-               (uint32_t)(S.ty * S.pitch * sizeof(T)));
-    bulk_commit();
-  };
-  for (int s = z0 - 1; s <= z1; ++s) {
-    // Thread 0 waits (bounded) for the inputs of stage s -- phi planes s-1..s+1 and rhs
-    // plane s -- while the other threads wait at the barrier instead of polling; after it,
-    // thread 0 stores plane s-2 (black-updated in the previous stage) and queues the loads
-    // for later stages into buffers whose stores have finished reading.
-    if (tid == 0) {
-      for (int p = (s == z0 - 1 ? z0 - 2 : s + 1); p <= s + 1; ++p)
-        if (!mbar_wait_bounded(&pbar[pslot(p)], pphase(p))) ok = false;
-      if (!mbar_wait_bounded(&rbar[rslot(s)], rphase(s))) ok = false;
-      if (ok) {
-        p_done = s + 1;
-        r_done = s;
-      }
-      s_ok = ok;
-    }
-    // every thread has finished stage s-1 (black plane s-2, fenced) and the inputs landed
-    __syncthreads();
-    if (!s_ok) {
-      if (tid == 0) atomicExch(err, 1);
-      break;
-    }
-    if (tid == 0) {
-      if (s - 2 >= z0) store_plane(s - 2);
-      bulk_wait_read1();  // the slot refilled below was stored two stages ago
-      if (s > z0 - 1) {
-        issue_phi(s + D);
-        issue_rhs(s + D - 1);
-      }
-    }
-
+  for (int s = s_first; s <= s_last; ++s) {
+    // inputs of stage s: phi planes s-1..s+1 (and s-2 for the black pass), rhs s and s-1;
+    // waits on landed phases return at once
+    bool ok = true;
+    for (int p = (s == s_first ? z0 - 2 : s + 1); p <= s + 1; ++p)
+      ok = ok && mbar_wait_bounded(&pbar[pslot(p)], pphase(p));
+    ok = ok && mbar_wait_bounded(&rbar[rslot(s)], rphase(s));
+    if (ok) {
     // Stage s red-updates plane s and black-updates plane s-1.  Both passes map (row, x) to
     // the same thread, and the red cell (x, y, s) sits right above the black cell
     // (x, y, s-1): the red update reads that black cell's old value, the black update reads
@@ -342,7 +372,7 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsi
     // black update of x = 0 / nx-1 in the next stage), one thread per row
     if (red && !ghost_plane) {
       const bool lo_in = !(S.flags & 1), hi_in = !(S.flags & 8);
-      for (int y = ya + tid; y <= yb; y += blockDim.x) {
+      for (int y = ya + tid; y <= yb; y += kConsumers) {
         if (y < 0 || y >= S.ny) continue;
         const int gy = S.loy + y;
         const int orow = (y - S.y0 + 2) * S.pitch + S.g;
@@ -361,20 +391,15 @@ __global__ void __launch_bounds__(256) k_rbgs_fused(UnitList L, int ty_max, unsi
         }
       }
     }
-    fence_async_smem();  // make the generic-proxy writes visible to the bulk stores
+      fence_async_smem();  // make the generic-proxy writes visible to the bulk stores
+    }
+    // stage s finished by every consumer; a wait that expired anywhere ends the CTA's work
+    if (consumer_sync_or(!ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      break;
+    }
+    if (tid == 0) mbar_arrive(&sbar[(s - s_first) % kStageBars]);
   }
-  // the last finished plane (z1-1) is stored after the loop
-  __syncthreads();
-  if (tid == 0 && s_ok && z1 - 1 >= z0) store_plane(z1 - 1);
-  // Drain: wait (bounded) for every load this CTA issued but did not consume -- at most
-  // D + 2 per ring, so each slot holds one outstanding phase -- and for the stores, so no
-  // copy touches shared memory after the CTA exits.
-  if (tid == 0) {
-    for (int p = p_done + 1; p <= p_issued; ++p) mbar_wait_bounded(&pbar[pslot(p)], pphase(p));
-    for (int p = r_done + 1; p <= r_issued; ++p) mbar_wait_bounded(&rbar[rslot(p)], rphase(p));
-    bulk_wait_all();
-  }
-  __syncthreads();
 }
 
 template <class T, int D>
@@ -386,7 +411,7 @@ static cudaError_t launch_fused_t(const UnitList& L, long long nunits, int ty, i
   const unsigned align = 128 / sizeof(T);
   pe = (pe + align - 1) / align * align;
   re = (re + align - 1) / align * align;
-  size_t smem = ((size_t)NP * pe + (size_t)NR * re) * sizeof(T) + (NP + NR) * 8;
+  size_t smem = ((size_t)NP * pe + (size_t)NR * re) * sizeof(T) + (NP + NR + kStageBars) * 8;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   static size_t opted_in = 0;  // largest dynamic shared memory size already allowed
   if (smem > opted_in) {
@@ -395,7 +420,7 @@ static cudaError_t launch_fused_t(const UnitList& L, long long nunits, int ty, i
     if (e != cudaSuccess) return e;
     opted_in = smem;
   }
-  k_rbgs_fused<T, D><<<(unsigned)nunits, 256, smem, s>>>(L, ty, pe, re, err);
+  k_rbgs_fused<T, D><<<(unsigned)nunits, kFusedThreads, smem, s>>>(L, ty, pe, re, err);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -406,7 +431,7 @@ size_t fused_smem_bytes(int dt, int ty, int max_pitch, int max_pitch_r, int dept
   size_t align = 128 / es;
   size_t pe = ((size_t)(ty + 4) * max_pitch + align - 1) / align * align;
   size_t re = ((size_t)(ty + 2) * max_pitch_r + align - 1) / align * align;
-  return (NP * pe + NR * re) * es + (NP + NR) * 8;
+  return (NP * pe + NR * re) * es + (NP + NR + kStageBars) * 8;
 }
 
 cudaError_t launch_rbgs_fused_l(int dt, const UnitList& L, long long nunits, int ty, int depth,
