@@ -139,26 +139,36 @@ def max_over_ranks(x, world):
 
 # ---- our arm --------------------------------------------------------------------------------
 
+# Source files whose contents define each profiled kernel (its launch configuration included).
+KERNEL_SOURCES = {
+    "rbgs_half_f64": ["mg_kernels.cu", "mg_kernels.hpp"],
+    "rbgs_fused_f32": ["mg_fused.cu", "mg_kernels.hpp", "mg_runtime.cu"],
+    "copy_tags_f64": ["mg_kernels.cu", "mg_kernels.hpp", "mg_runtime.cu"],
+}
+
+
+def kernel_source_hash(kernel):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2403_12179_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def roofline_traffic(kernel, workload):
     """dram bytes per launch from the committed ncu summary, if it was taken on the current
     kernel source (the summary records the source hash); else None."""
-    import hashlib
     p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(p):
         return None
-    src = os.path.join(ROOT, "paper_2403_12179_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".hpp")):
-            h.update(open(os.path.join(src, f), "rb").read())
-    cur = h.hexdigest()[:16]
     traffic = src_hash = None
     for line in open(p):
         if line.startswith("traffic_bytes_per_launch:"):
             traffic = float(line.split(":")[1])
         if line.startswith("source_hash:"):
             src_hash = line.split(":")[1].strip()
-    return traffic if src_hash == cur else None
+    return traffic if src_hash == kernel_source_hash(kernel) else None
 
 
 def run_ours(args, wl_name):
@@ -630,7 +640,7 @@ def run_fill(args):
                         "fused_speedup": round(t_unfused / t, 2)},
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
-                         "peak_source": src}}
+                         "peak_source": src, "traffic": roofline_traffic("copy_tags_f64", "fill")}}
     mg.mg_finalize(ctx)
     print(json.dumps(line), flush=True)
 
