@@ -80,6 +80,11 @@ typedef struct {
                          the bottom run as ONE launch per V-cycle (one CTA per solve, levels
                          held in shared memory; same arithmetic, bit-identical results).
                          0 (default): 512 for FP64 levels, 4096 for FP32 levels; -1: off */
+  int direct_reads;   /* 1 (default): on levels whose boxes form a regular grid, the
+                         smoother, residual and residual+restriction read the neighbouring
+                         boxes (or the periodic image, or the negated boundary cell across a
+                         Dirichlet face) directly instead of first filling one ghost layer:
+                         the same values, without the fill launches.  0: always fill. */
 } mg_options;
 
 typedef struct {
@@ -267,7 +272,7 @@ int mg_bottom_solve(mg_ctx_t ctx, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, d
  * h <= 0 means 1 / (domain x extent).  The norm is written to the host double *norm; the
  * call synchronises `stream`.
  * Scratch: a file-scope device array of 1024 box-table rows plus an 8-byte accumulator
- * (229,632 bytes), held by every GPU that loads the library until the process exits; no
+ * (278,784 bytes), held by every GPU that loads the library until the process exits; no
  * cudaMalloc, cudaFree or pool allocation happens in this call.  At most 1024 boxes
  * (MG_EINVAL beyond).  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any stream

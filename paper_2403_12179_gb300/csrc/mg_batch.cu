@@ -54,8 +54,10 @@ struct SegB {
   std::vector<Seg> v;
   long long total = 0;
   size_t off = 0;
+  bool direct = false;  // some member's rows carry box-face reads
   void add(const OpTable& t, int slot) {
     if (!t.nrows) return;
+    direct = direct || t.direct;
     Seg s{};
     s.rows = t.rows();
     s.row_begin = total;
@@ -201,9 +203,9 @@ void build_lists(Ctx& c, StepLists& S, const std::vector<Member*>& run,
         LL.fill_rhs.add(fill_plan(c, *D.rhs, &H.bc, 1), D.rhs->base);
       } else {
         LL.half.add(D.smooth, m->slot);
-        LL.fill1_half.add(fill_plan(c, *D.phi, &H.bc, 1), D.phi->base);
+        if (!D.direct) LL.fill1_half.add(fill_plan(c, *D.phi, &H.bc, 1), D.phi->base);
       }
-      LL.fill1_all.add(fill_plan(c, *D.phi, &H.bc, 1), D.phi->base);
+      if (!D.direct) LL.fill1_all.add(fill_plan(c, *D.phi, &H.bc, 1), D.phi->base);
       LL.half_all.add(D.smooth, m->slot);
       LL.rr.add(D.rr, m->slot);
       LL.prolong.add(D.prolong, m->slot);
@@ -217,7 +219,7 @@ void build_lists(Ctx& c, StepLists& S, const std::vector<Member*>& run,
   }
   for (Member* m : check) {
     S.resid0.add(m->H->resid0, m->slot);
-    S.fill_phi0.add(fill_plan(c, *m->H->phi0, &m->H->bc, 1), m->H->phi0->base);
+    if (!m->H->direct0) S.fill_phi0.add(fill_plan(c, *m->H->phi0, &m->H->bc, 1), m->H->phi0->base);
   }
   for (Member* m : fresh) S.rhsabs0.add(m->H->rhsabs0, m->slot);
 }
@@ -270,14 +272,15 @@ void smooth_l(Ctx& c, StepLists& S, LevelLists& LL, int sweeps, const unsigned c
       for (int j = 0; j < 2; ++j)
         for (int color = 0; color < 2; ++color) {
           fill_l(c, S.dt, LL.fill1_half, dev, s);
-          MG_CK(launch_rbgs_half_l(S.dt, mk(LL.half, dev), LL.half.total, color, s));
+          MG_CK(launch_rbgs_half_l(S.dt, mk(LL.half, dev), LL.half.total, color, s, LL.half.direct));
         }
   }
   for (; k < sweeps; ++k)
     for (int color = 0; color < 2; ++color) {
       // an odd sweep: every member with half-sweeps (fused members too, in place)
       fill_l(c, S.dt, LL.fill1_all, dev, s);
-      MG_CK(launch_rbgs_half_l(S.dt, mk(LL.half_all, dev), LL.half_all.total, color, s));
+      MG_CK(launch_rbgs_half_l(S.dt, mk(LL.half_all, dev), LL.half_all.total, color, s,
+                               LL.half_all.direct));
     }
 }
 
@@ -301,7 +304,7 @@ void enqueue_step(Ctx& c, StepLists& S, const unsigned char* dev, unsigned long 
     if (LL.fill_rhs.total) fill_l(c, S.dt, LL.fill_rhs, dev, s);
     smooth_l(c, S, LL, S.nu1, dev, err, s);
     fill_l(c, S.dt, LL.fill1_all, dev, s);
-    MG_CK(launch_residual_restrict_l(S.dt, mk(LL.rr, dev), LL.rr.total, s));
+    MG_CK(launch_residual_restrict_l(S.dt, mk(LL.rr, dev), LL.rr.total, s, LL.rr.direct));
     if (!LL.bottom_next.v.empty())
       MG_CK(launch_bottom(S.dt, (const BottomJob*)(dev + LL.bottom_next.off),
                           (int)LL.bottom_next.v.size(), LL.bottom_next.maxN, s));
@@ -322,7 +325,7 @@ void enqueue_step(Ctx& c, StepLists& S, const unsigned char* dev, unsigned long 
   if (any_fresh && S.rhsabs0.total)
     MG_CK(launch_maxabs_l(DT_F64, mk(S.rhsabs0, dev), S.rhsabs0.total, norms, s));
   fill_l(c, DT_F64, S.fill_phi0, dev, s);
-  if (S.resid0.total) MG_CK(launch_residual_l(DT_F64, mk(S.resid0, dev), S.resid0.total, norms, s));
+  if (S.resid0.total) MG_CK(launch_residual_l(DT_F64, mk(S.resid0, dev), S.resid0.total, norms, s, S.resid0.direct));
 }
 
 // Applies the stop rule of a single solve to a member after its norm check.

@@ -131,7 +131,8 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
   return v;
 }
 
-// Sum of the six neighbours of p[0] in the order x-, x+, y-, y+, z-, z+.
+// Sum of the six neighbours of p[0] in the order x-, x+, y-, y+, z-, z+ (ghost cells read as
+// they are).
 template <class T>
 __device__ __forceinline__ T nbr_sum(const T* p, int pitch, long long plane) {
   T s = p[-1];
@@ -148,7 +149,68 @@ __device__ __forceinline__ T* line(const DView& v, int y, int z) {
   return (T*)v.p + (long long)z * v.plane + (long long)y * v.pitch;
 }
 
-// ---------------------------------------------------------------------------------------
+// Neighbour rows of row (y, z) of v[0] for the stencil kernels, with the box-face reads of
+// DRow::nbd / nbf applied (ghost cells when those are zero).  Negations are applied as XORs of
+// the sign bit with a runtime 0/1 flag, so they never turn into extra floating-point work.
+template <class T>
+struct Nbr {
+  const T* ym;
+  const T* yp;
+  const T* zm;
+  const T* zp;
+  long long dxm, dxp;  // x- at x = 0, x+ at x = nx-1
+  unsigned neg;        // bit f: negate face f's reads (x-, x+, y-, y+, z-, z+) in this row
+};
+__device__ __forceinline__ double xsign(double v, unsigned n) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)n << 63));
+}
+__device__ __forceinline__ float xsign(float v, unsigned n) {
+  return __int_as_float(__float_as_int(v) ^ (int)(n << 31));
+}
+
+template <class T>
+__device__ __forceinline__ Nbr<T> nbr_rows(const DRow& R, const T* row, int y, int z) {
+  const int pitch = R.v[0].pitch;
+  const long long plane = R.v[0].plane;
+  const unsigned f = (unsigned)R.nbf;
+  const bool y0 = y == 0, y1 = y == R.n[1] - 1, z0 = z == 0, z1 = z == R.n[2] - 1;
+  Nbr<T> b;
+  b.ym = row - pitch + (y0 ? R.nbd[2] : 0);
+  b.yp = row + pitch + (y1 ? R.nbd[3] : 0);
+  b.zm = row - plane + (z0 ? R.nbd[4] : 0);
+  b.zp = row + plane + (z1 ? R.nbd[5] : 0);
+  b.dxm = R.nbd[0];
+  b.dxp = R.nbd[1];
+  b.neg = (f & 3u) | (y0 ? f & 4u : 0u) | (y1 ? f & 8u : 0u) | (z0 ? f & 16u : 0u) |
+          (z1 ? f & 32u : 0u);
+  return b;
+}
+
+// The six-neighbour sum of cell x of `row` (order x-, x+, y-, y+, z-, z+) through Nbr.
+// NEG = false: the row has no negated reads (interior and periodic faces: the common case,
+// decided per row so that a warp takes one branch).
+template <bool NEG, class T>
+__device__ __forceinline__ T nbr_sum_rows(const T* row, int x, int nx, const Nbr<T>& b) {
+  const bool e0 = x == 0, e1 = x == nx - 1;
+  T xm = row[x - 1 + (e0 ? b.dxm : 0)];
+  T xp = row[x + 1 + (e1 ? b.dxp : 0)];
+  T ym = b.ym[x], yp = b.yp[x], zm = b.zm[x], zp = b.zp[x];
+  if (NEG) {
+    xm = xsign(xm, e0 ? b.neg & 1u : 0u);
+    xp = xsign(xp, e1 ? (b.neg >> 1) & 1u : 0u);
+    ym = xsign(ym, (b.neg >> 2) & 1u);
+    yp = xsign(yp, (b.neg >> 3) & 1u);
+    zm = xsign(zm, (b.neg >> 4) & 1u);
+    zp = xsign(zp, (b.neg >> 5) & 1u);
+  }
+  T s = Ar<T>::add(xm, xp);
+  s = Ar<T>::add(s, ym);
+  s = Ar<T>::add(s, yp);
+  s = Ar<T>::add(s, zm);
+  s = Ar<T>::add(s, zp);
+  return s;
+}
+
 // Copy tags (ghost fill).  One warp per chunk of whole x-rows of one tag (tag_chunk_rows).
 // Segments = fabs.  Sources are valid cells and destinations ghost cells, never the same
 // memory within a launch, so sources are read through the read-only path.
@@ -209,21 +271,33 @@ __global__ void __launch_bounds__(256) k_copy_tags(TagList L, long long nchunks,
 // ---------------------------------------------------------------------------------------
 // Red-black Gauss-Seidel half-sweep: cells with (i+j+k) mod 2 == color (global indices)
 // take phi = (s - h^2 rhs) / 6.  Lane l of a warp updates cells par + 2l (+64 k) of a line.
-template <class T>
-__global__ void __launch_bounds__(kThreads, 6) k_rbgs_half(SegList L, long long nrows, long long per,
+// DIRECT: box-face neighbours through DRow::nbd / nbf (rows without that information read
+// their ghost cells); else ghost cells, through plain offsets.
+template <class T, bool DIRECT>
+__global__ void __launch_bounds__(kThreads, DIRECT ? 4 : 6) k_rbgs_half(SegList L, long long nrows, long long per,
                                                         int color) {
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)(lr % n1), z = (int)(lr / n1);
-    const DView vp = R.v[0];
-    T* phi = line<T>(vp, y, z);
+    T* phi = line<T>(R.v[0], y, z);
     const T* rhs = line<T>(R.v[1], y, z);
     const T h2 = (T)R.h2;
     const int par = (color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1;
-    for (int x = par + 2 * lane; x < n0; x += 64) {
-      T s = nbr_sum(phi + x, vp.pitch, vp.plane);
-      phi[x] = gs_update(s, rhs[x], h2);
+    if constexpr (DIRECT) {
+      const Nbr<T> nb = nbr_rows<T>(R, phi, y, z);
+      if (nb.neg == 0) {
+        for (int x = par + 2 * lane; x < n0; x += 64)
+          phi[x] = gs_update(nbr_sum_rows<false>(phi, x, n0, nb), rhs[x], h2);
+      } else {
+        for (int x = par + 2 * lane; x < n0; x += 64)
+          phi[x] = gs_update(nbr_sum_rows<true>(phi, x, n0, nb), rhs[x], h2);
+      }
+    } else {
+      const int pitch = R.v[0].pitch;
+      const long long plane = R.v[0].plane;
+      for (int x = par + 2 * lane; x < n0; x += 64)
+        phi[x] = gs_update(nbr_sum(phi + x, pitch, plane), rhs[x], h2);
     }
   });
 }
@@ -255,8 +329,8 @@ __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
 
 // Residual r = rhs - (s - 6 phi) / h^2, optionally stored, with a fused max-norm into
 // norms[slot + solve].
-template <class T>
-__global__ void __launch_bounds__(kThreads, 6) k_residual(SegList L, long long nrows, long long per,
+template <class T, bool DIRECT>
+__global__ void __launch_bounds__(kThreads, DIRECT ? 4 : 6) k_residual(SegList L, long long nrows, long long per,
                                                        unsigned long long* norms) {
   const int lane = threadIdx.x & 31;
   unsigned long long mx = 0;
@@ -273,17 +347,25 @@ __global__ void __launch_bounds__(kThreads, 6) k_residual(SegList L, long long n
     }
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)(lr % n1), z = (int)(lr / n1);
-    const DView vp = R.v[0];
-    const T* phi = line<T>(vp, y, z);
+    const T* phi = line<T>(R.v[0], y, z);
     const T* rhs = line<T>(R.v[1], y, z);
     T* r = R.v[2].p ? line<T>(R.v[2], y, z) : nullptr;
     const T ih2 = (T)R.ih2;
-    for (int x = lane; x < n0; x += 32) {
-      T s = nbr_sum(phi + x, vp.pitch, vp.plane);
+    const Nbr<T> nb = DIRECT ? nbr_rows<T>(R, phi, y, z) : Nbr<T>{};
+    auto cell = [&](int x, T s) {
       T v = residual_of(s, phi[x], rhs[x], ih2);
       if (r) r[x] = v;
       unsigned long long k = Ar<T>::abskey(v);
       mx = k > mx ? k : mx;
+    };
+    if constexpr (DIRECT) {
+      if (nb.neg == 0) {
+        for (int x = lane; x < n0; x += 32) cell(x, nbr_sum_rows<false>(phi, x, n0, nb));
+      } else {
+        for (int x = lane; x < n0; x += 32) cell(x, nbr_sum_rows<true>(phi, x, n0, nb));
+      }
+    } else {
+      for (int x = lane; x < n0; x += 32) cell(x, nbr_sum(phi + x, R.v[0].pitch, R.v[0].plane));
     }
   });
   if (norms) flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
@@ -291,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_residual(SegList L, long long n
 
 // Fused residual + restriction.  Lane l of a warp produces coarse cells X = l, l+32, ... of
 // one coarse x-line: the 8 child residuals summed x fastest, times 1/8.
-template <class T>
+template <class T, bool DIRECT>
 __global__ void __launch_bounds__(kThreads) k_residual_restrict(SegList L, long long nrows,
                                                                 long long per) {
   const int lane = threadIdx.x & 31;
@@ -302,20 +384,25 @@ __global__ void __launch_bounds__(kThreads) k_residual_restrict(SegList L, long 
     const T ih2 = (T)R.ih2;
     T* crhs = line<T>(R.c[0], Y, Z);
     T* cphi = R.c[1].p ? line<T>(R.c[1], Y, Z) : nullptr;
+    const int n0 = R.n[0];
     for (int X = lane; X < nc0; X += 32) {
       T acc = T(0);
 #pragma unroll
       for (int k = 0; k < 2; ++k)
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+        for (int j = 0; j < 2; ++j) {
+          const T* row = line<T>(vp, 2 * Y + j, 2 * Z + k);
+          const Nbr<T> nb = DIRECT ? nbr_rows<T>(R, row, 2 * Y + j, 2 * Z + k) : Nbr<T>{};
 #pragma unroll
           for (int i = 0; i < 2; ++i) {
-            const T* p = line<T>(vp, 2 * Y + j, 2 * Z + k) + 2 * X + i;
             const T* q = line<T>(vr, 2 * Y + j, 2 * Z + k) + 2 * X + i;
-            T s = nbr_sum(p, vp.pitch, vp.plane);
-            T v = residual_of(s, p[0], q[0], ih2);
+            T s = !DIRECT ? nbr_sum(row + 2 * X + i, vp.pitch, vp.plane)
+                          : nb.neg ? nbr_sum_rows<true>(row, 2 * X + i, n0, nb)
+                                   : nbr_sum_rows<false>(row, 2 * X + i, n0, nb);
+            T v = residual_of(s, row[2 * X + i], q[0], ih2);
             acc = (i | j | k) ? Ar<T>::add(acc, v) : v;
           }
+        }
       crhs[X] = Ar<T>::mul(acc, (T)0.125);
       if (cphi) cphi[X] = T(0);
     }
@@ -536,6 +623,16 @@ int num_sms() {
     if ((dt) == DT_F64) KERNEL<double><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);    \
     else KERNEL<float><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);                    \
   } while (0)
+#define GB_DISPATCH_D(dt, direct, KERNEL, GRID, BLOCK, SMEM, STREAM, ...)                  \
+  do {                                                                                   \
+    if ((dt) == DT_F64) {                                                                \
+      if (direct) KERNEL<double, true><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);       \
+      else KERNEL<double, false><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);             \
+    } else {                                                                             \
+      if (direct) KERNEL<float, true><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);        \
+      else KERNEL<float, false><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);              \
+    }                                                                                    \
+  } while (0)
 
 cudaError_t launch_copy_tags_l(int dt, const TagList& L, long long nchunks, int ncomp, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
@@ -563,27 +660,28 @@ cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int n
   return launch_copy_tags_l(dt, L, nchunks, ncomp, s);
 }
 
-cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int color, cudaStream_t s) {
+cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int color, cudaStream_t s,
+                               bool direct) {
   if (nrows <= 0) return cudaSuccess;
   Grid g = row_grid(nrows, 16);
-  GB_DISPATCH(dt, k_rbgs_half, g.blocks, kThreads, 0, s, L, nrows, g.per, color);
+  GB_DISPATCH_D(dt, direct, k_rbgs_half, g.blocks, kThreads, 0, s, L, nrows, g.per, color);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool direct) {
   if (nrows <= 0) return cudaSuccess;
   Grid g = row_grid(nrows, 16);
-  GB_DISPATCH(dt, k_residual, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
+  GB_DISPATCH_D(dt, direct, k_residual, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s) {
+cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s, bool direct) {
   if (nrows <= 0) return cudaSuccess;
   Grid g = row_grid(nrows, 16);
-  GB_DISPATCH(dt, k_residual_restrict, g.blocks, kThreads, 0, s, L, nrows, g.per);
+  GB_DISPATCH_D(dt, direct, k_residual_restrict, g.blocks, kThreads, 0, s, L, nrows, g.per);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -635,18 +733,18 @@ cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsign
 // ---- single-table launchers (one segment) ------------------------------------------------
 
 cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
-                             cudaStream_t s) {
-  return launch_rbgs_half_l(dt, one_seg(rows, nbox), nrows, color, s);
+                             cudaStream_t s, bool direct) {
+  return launch_rbgs_half_l(dt, one_seg(rows, nbox), nrows, color, s, direct);
 }
 
 cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
-                            unsigned long long* norms, cudaStream_t s) {
-  return launch_residual_l(dt, one_seg(rows, nbox), nrows, norms, s);
+                            unsigned long long* norms, cudaStream_t s, bool direct) {
+  return launch_residual_l(dt, one_seg(rows, nbox), nrows, norms, s, direct);
 }
 
 cudaError_t launch_residual_restrict(int dt, const DRow* rows, int nbox, long long nrows,
-                                     cudaStream_t s) {
-  return launch_residual_restrict_l(dt, one_seg(rows, nbox), nrows, s);
+                                     cudaStream_t s, bool direct) {
+  return launch_residual_restrict_l(dt, one_seg(rows, nbox), nrows, s, direct);
 }
 
 cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows, cudaStream_t s) {

@@ -37,6 +37,15 @@ struct DRow {
   double ih2;    // 1/(h*h)
   DView v[3];    // op-specific fine views (see each launcher)
   DView c[2];    // op-specific coarse views, addressing coarse cell floor(lo/2)
+  // Neighbour reads of the FP64 smoother / residual / residual+restriction kernels, per face
+  // x-, x+, y-, y+, z-, z+ of the box: a stencil value in the face's first ghost layer is read
+  // at (ghost cell + nbd[f]) elements of v[0], negated if bit f of nbf is set.  All zero: the
+  // ghost cells themselves (filled beforehand).  Set from the box array (direct_neighbours):
+  // the cell of the neighbouring box or periodic image that the fill would copy, or the box's
+  // own boundary cell (negated) across a Dirichlet face.
+  long long nbd[6];
+  int nbf;
+  int pad2_;
 };
 
 // Ghost-fill tag: destination cells dst + x + y*dsy + z*dsz (0 <= x < ex ...) take
@@ -158,19 +167,22 @@ long long launches_so_far();
 cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int nchunks,
                              void* base, int ncomp, cudaStream_t s);
 
-// v[0] = phi (ghosts filled), v[1] = rhs.
+// Stencil launchers: with direct = true the kernel reads box-face neighbours through
+// DRow::nbd / nbf (rows whose nbd / nbf are zero read their ghost cells); with false it reads
+// the ghost cells (filled beforehand) through plain offsets.
+// v[0] = phi, v[1] = rhs.
 cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
-                             cudaStream_t s);
+                             cudaStream_t s, bool direct = false);
 
 // v[0] = phi, v[1] = rhs, v[2] = r (p == null: not stored).  norms[solve] receives
 // atomicMax of the bit pattern of |r| (NaN propagates as the largest pattern).
 cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
-                            unsigned long long* norms, cudaStream_t s);
+                            unsigned long long* norms, cudaStream_t s, bool direct = false);
 
 // Rows are coarse x-lines.  v[0] = phi, v[1] = rhs (fine); c[0] = coarse rhs,
 // c[1] = coarse phi (p == null: not zeroed).
 cudaError_t launch_residual_restrict(int dt, const DRow* rows, int nbox, long long nrows,
-                                     cudaStream_t s);
+                                     cudaStream_t s, bool direct = false);
 
 // Rows are coarse x-lines.  v[0] = fine field; c[0] = coarse field.
 cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows, cudaStream_t s);
@@ -228,10 +240,12 @@ cudaError_t launch_correct_add(const DRow* rows, int nbox, long long nrows,
 // Launchers over segment lists (several solves per launch); nrows / nchunks / nunits are
 // the totals over all segments.
 cudaError_t launch_copy_tags_l(int dt, const TagList& L, long long nchunks, int ncomp, cudaStream_t s);
-cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int color, cudaStream_t s);
+cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int color, cudaStream_t s,
+                               bool direct = false);
 cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
-                              cudaStream_t s);
-cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s);
+                              cudaStream_t s, bool direct = false);
+cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s,
+                                       bool direct = false);
 cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cudaStream_t s);
 cudaError_t launch_set_valid_l(int dt, const SegList& L, long long nrows, double value, cudaStream_t s);
 cudaError_t launch_maxabs_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,

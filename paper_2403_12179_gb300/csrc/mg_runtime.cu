@@ -11,6 +11,8 @@
 #include <cstdlib>
 #include <sstream>
 
+#include <cmath>
+
 #include "mg_runtime.hpp"
 
 namespace gbmg {
@@ -259,6 +261,55 @@ void launch_fill(Ctx& c, FabObj& f, const mg_bc* bc, cudaStream_t s, int layers)
   MG_CK(launch_copy_tags(f.dtype, P.tags(), P.chunks(), P.nchunks(), f.base, f.lay.ncomp, s));
 }
 
+FaceReads direct_neighbours(const FabObj& f, const int periodic[3]) {
+  FaceReads out;
+  const BoxArray& ba = f.ba->ba;
+  const FabLayout& lay = f.lay;
+  const size_t nb = ba.boxes.size();
+  if (nb == 0 || lay.g < 1) return out;
+  int E[3];
+  for (int d = 0; d < 3; ++d) E[d] = ba.boxes[0].len(d);
+  std::map<std::array<int, 3>, int> at_lo;
+  for (size_t b = 0; b < nb; ++b) {
+    const Box& B = ba.boxes[b];
+    for (int d = 0; d < 3; ++d)
+      if (B.len(d) != E[d] || (B.lo[d] - ba.dom.lo[d]) % E[d] != 0) return out;
+    if (lay.pitch[b] != lay.pitch[0] || lay.plane[b] != lay.plane[0]) return out;
+    at_lo[{B.lo[0], B.lo[1], B.lo[2]}] = (int)b;
+  }
+  std::vector<std::array<long long, 6>> dl(nb);
+  std::vector<int> fl(nb, 0);
+  for (size_t b = 0; b < nb; ++b) {
+    const Box& B = ba.boxes[b];
+    const long long stride[3] = {1, lay.pitch[b], lay.plane[b]};
+    for (int d = 0; d < 3; ++d)
+      for (int side = 0; side < 2; ++side) {
+        const int face = 2 * d + side;
+        int g[3] = {B.lo[0], B.lo[1], B.lo[2]};  // low corner of the first ghost layer
+        g[d] = side ? B.hi[d] + 1 : B.lo[d] - 1;
+        const long long ghost = lay.at(ba, (int)b, g[0], g[1], g[2]);
+        const int L = ba.dom.len(d);
+        if (g[d] < ba.dom.lo[d] || g[d] > ba.dom.hi[d]) {
+          if (!periodic[d]) {  // -(the box's own boundary layer)
+            dl[b][face] = side ? -stride[d] : stride[d];
+            fl[b] |= 1 << face;
+            continue;
+          }
+          g[d] += g[d] < ba.dom.lo[d] ? L : -L;
+        }
+        std::array<int, 3> lo;
+        for (int k = 0; k < 3; ++k)
+          lo[k] = ba.dom.lo[k] + (int)std::floor((double)(g[k] - ba.dom.lo[k]) / E[k]) * E[k];
+        auto it = at_lo.find(lo);
+        if (it == at_lo.end()) return FaceReads{};
+        dl[b][face] = lay.at(ba, it->second, g[0], g[1], g[2]) - ghost;
+      }
+  }
+  out.d = std::move(dl);
+  out.flags = std::move(fl);
+  return out;
+}
+
 OpTable upload_table(Ctx& c, const std::vector<DRow>& rows, long long nrows, cudaStream_t s) {
   OpTable t;
   t.nbox = (int)rows.size();
@@ -487,6 +538,7 @@ SolveParams params_from(const mg_options* o, const BoxArray& ba) {
     p.fixed_vcycles = o->fixed_vcycles;
     p.h = o->h;
     p.coarse_cells = o->coarse_cells;
+    p.direct_reads = o->direct_reads;
   }
   if (p.h <= 0.0) p.h = 1.0 / ba.dom.len(0);
   if (p.nu1 < 0 || p.nu2 < 0 || p.max_iter < 0 || p.nu1 + p.nu2 == 0)

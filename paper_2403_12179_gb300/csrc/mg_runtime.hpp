@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -109,10 +110,28 @@ struct FabObj {
   int esize() const { return dtype == DT_F64 ? 8 : 4; }
 };
 
+// Face reads of the stencil kernels (DRow::nbd / nbf) for the boxes of fab f under the given
+// BCs.  Returns false, leaving `out` empty, unless the boxes form a regular grid (equal
+// extents on a lattice anchored at the domain's low corner) with one layout, so that each
+// face's first ghost layer is exactly one face layer of one box (or its periodic image), or
+// lies across a Dirichlet face; the kernels must then read filled ghost cells.
+struct FaceReads {
+  std::vector<std::array<long long, 6>> d;
+  std::vector<int> flags;
+  bool ok() const { return !d.empty(); }
+  void apply(int b, DRow& R) const {
+    if (!ok()) return;
+    for (int f = 0; f < 6; ++f) R.nbd[f] = d[b][f];
+    R.nbf = flags[b];
+  }
+};
+FaceReads direct_neighbours(const FabObj& f, const int periodic[3]);
+
 struct OpTable {
   DevBufP d;
   int nbox = 0;
   long long nrows = 0;
+  bool direct = false;  // rows carry box-face reads (DRow::nbd / nbf)
   const DRow* rows() const { return d ? (const DRow*)d->p : nullptr; }
 };
 
@@ -263,7 +282,7 @@ std::vector<DTag> device_tags(const BoxArray& ba, const FabLayout& lay,
 // Hierarchy / solve -----------------------------------------------------------------------
 struct SolveParams {
   int nu1 = 2, nu2 = 2, max_iter = 50, precision = MG_PREC_F64, smoother = MG_SMOOTH_AUTO;
-  int use_graph = 1, fixed_vcycles = -1, coarse_cells = 0;
+  int use_graph = 1, fixed_vcycles = -1, coarse_cells = 0, direct_reads = 1;
   double h = 0.0;
 };
 SolveParams params_from(const mg_options* o, const BoxArray& ba);

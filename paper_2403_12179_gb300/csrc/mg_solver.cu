@@ -58,17 +58,23 @@ namespace {
 
 void build_tables(Ctx& c, Hierarchy& H, cudaStream_t s) {
   const int nl = (int)H.L.size();
+  int per[3];
+  bc_code(&H.bc, per);
   for (int l = 0; l < nl; ++l) {
     LevelData& D = H.L[l];
     const BoxArray& ba = D.bao->ba;
+    // levels smoothed by half-sweeps may read neighbouring boxes instead of ghost cells
+    FaceReads fr;
+    if (H.p.direct_reads && !D.fused) fr = direct_neighbours(*D.phi, per);
+    D.direct = fr.ok();
     D.smooth = make_table(c, ba, 0, D.h, 0, [&](int b, DRow& R) {
       R.v[0] = D.phi->view(b);
       R.v[1] = D.rhs->view(b);
+      fr.apply(b, R);
     }, s);
+    D.smooth.direct = D.direct;
     D.zero = make_table(c, ba, 0, D.h, 0, [&](int b, DRow& R) { R.v[0] = D.phi->view(b); }, s);
     if (D.fused) {
-      int per[3];
-      bc_code(&H.bc, per);
       D.f_ab = make_fused(c, ba, D.h, *D.phi, *D.rhs, *D.phi2, per, s);
       D.f_ba = make_fused(c, ba, D.h, *D.phi2, *D.rhs, *D.phi, per, s);
       if (!D.f_ab.ok || !D.f_ba.ok) D.fused = false;
@@ -80,7 +86,9 @@ void build_tables(Ctx& c, Hierarchy& H, cudaStream_t s) {
         R.v[1] = D.rhs->view(b);
         R.c[0] = coarse_view_of(*C.rhs, ba.boxes[b]);
         R.c[1] = coarse_view_of(*C.phi, ba.boxes[b]);
+        fr.apply(b, R);
       }, s);
+      D.rr.direct = D.direct;
       D.prolong = make_table(c, ba, 0, D.h, 0, [&](int b, DRow& R) {
         R.v[0] = D.phi->view(b);
         R.c[0] = coarse_view_of(*C.phi, ba.boxes[b]);
@@ -90,11 +98,16 @@ void build_tables(Ctx& c, Hierarchy& H, cudaStream_t s) {
   // level-0 FP64 tables: norm check (and the mixed-precision scale / correction)
   const BoxArray& ba0 = H.L[0].bao->ba;
   const double h0 = H.L[0].h;
+  FaceReads fr0;
+  if (H.p.direct_reads) fr0 = direct_neighbours(*H.phi0, per);
+  H.direct0 = fr0.ok();
   H.resid0 = make_table(c, ba0, 0, h0, 0, [&](int b, DRow& R) {
     R.v[0] = H.phi0->view(b);
     R.v[1] = H.rhs0->view(b);
     if (H.mixed) R.v[2] = H.r0->view(b);  // kept for the next outer iteration's scaling
+    fr0.apply(b, R);
   }, s);
+  H.resid0.direct = H.direct0;
   H.rhsabs0 = make_table(c, ba0, 0, h0, 1, [&](int b, DRow& R) { R.v[0] = H.rhs0->view(b); }, s);
   H.zero0_64 = make_table(c, ba0, 0, h0, 0, [&](int b, DRow& R) { R.v[0] = H.phi0->view(b); }, s);
   if (H.mixed) {
@@ -111,8 +124,6 @@ void build_tables(Ctx& c, Hierarchy& H, cudaStream_t s) {
   // bottom
   const LevelData& B = H.L.back();
   const BoxArray& bb = B.bao->ba;
-  int per[3];
-  bc_code(&H.bc, per);
   int n[3] = {bb.dom.len(0), bb.dom.len(1), bb.dom.len(2)};
   const std::vector<double>& Mt = bottom_matrix_t(c, n, per, B.h);
   long long N = bb.dom.npts();
@@ -224,7 +235,7 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
     if (h->rhs_id == rhs.id && h->phi_id == phi.id && h->bc_key == key &&
         h->p.nu1 == p.nu1 && h->p.nu2 == p.nu2 && h->p.precision == p.precision &&
         h->p.smoother == p.smoother && h->p.h == p.h &&
-        h->p.coarse_cells == p.coarse_cells)
+        h->p.coarse_cells == p.coarse_cells && h->p.direct_reads == p.direct_reads)
       return *h;
   }
   if (rhs.dtype != DT_F64 || phi.dtype != DT_F64) fail(MG_EINVAL, "mg_solve needs FP64 fabs");
@@ -299,8 +310,9 @@ void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s) {
   }
   for (; k < sweeps; ++k)
     for (int color = 0; color < 2; ++color) {
-      launch_fill(c, *D.phi, &H.bc, s, 1);  // the 7-point half-sweep reads one layer
-      MG_CK(launch_rbgs_half(H.dt, D.smooth.rows(), D.smooth.nbox, D.smooth.nrows, color, s));
+      if (!D.direct) launch_fill(c, *D.phi, &H.bc, s, 1);  // the half-sweep reads one layer
+      MG_CK(launch_rbgs_half(H.dt, D.smooth.rows(), D.smooth.nbox, D.smooth.nrows, color, s,
+                             D.direct));
     }
 }
 
@@ -311,8 +323,8 @@ void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s) {
     LevelData& D = H.L[l];
     if (D.fused) launch_fill(c, *D.rhs, &H.bc, s, 1);  // rhs ghosts for the redundant ring
     smooth(c, H, D, H.p.nu1, s);
-    launch_fill(c, *D.phi, &H.bc, s, 1);
-    MG_CK(launch_residual_restrict(H.dt, D.rr.rows(), D.rr.nbox, D.rr.nrows, s));
+    if (!D.direct) launch_fill(c, *D.phi, &H.bc, s, 1);
+    MG_CK(launch_residual_restrict(H.dt, D.rr.rows(), D.rr.nbox, D.rr.nrows, s, D.direct));
   }
   if (H.lc < nl) MG_CK(launch_coarse_cycle(H.dt, (const CoarseJob*)H.cjob->p, 1, H.csmem, s));
   else MG_CK(launch_bottom(H.dt, (const BottomJob*)H.job->p, 1, H.N, s));
@@ -333,8 +345,8 @@ void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
   if (H.mixed)
     MG_CK(launch_correct_add(H.correct0.rows(), H.correct0.nbox, H.correct0.nrows, dn, s));
   MG_CK(cudaMemsetAsync(dn, 0, 8, s));
-  launch_fill(c, *H.phi0, &H.bc, s, 1);
-  MG_CK(launch_residual(DT_F64, H.resid0.rows(), H.resid0.nbox, H.resid0.nrows, dn, s));
+  if (!H.direct0) launch_fill(c, *H.phi0, &H.bc, s, 1);
+  MG_CK(launch_residual(DT_F64, H.resid0.rows(), H.resid0.nbox, H.resid0.nrows, dn, s, H.direct0));
   MG_CK(cudaMemcpyAsync(H.hnorm, dn, 16, cudaMemcpyDeviceToHost, s));
 }
 
@@ -412,8 +424,8 @@ int solve(Ctx& c, int64_t rhs_id, int64_t phi_id, const mg_bc* bc, double tol,
   // ||rhs||_inf and the first residual norm
   MG_CK(cudaMemsetAsync(dn, 0, 16, s));
   MG_CK(launch_maxabs(DT_F64, H.rhsabs0.rows(), H.rhsabs0.nbox, H.rhsabs0.nrows, dn, s));
-  launch_fill(c, *H.phi0, bc, s, 1);
-  MG_CK(launch_residual(DT_F64, H.resid0.rows(), H.resid0.nbox, H.resid0.nrows, dn, s));
+  if (!H.direct0) launch_fill(c, *H.phi0, bc, s, 1);
+  MG_CK(launch_residual(DT_F64, H.resid0.rows(), H.resid0.nbox, H.resid0.nrows, dn, s, H.direct0));
   MG_CK(cudaMemcpyAsync(H.hnorm, dn, 16, cudaMemcpyDeviceToHost, s));
   MG_CK(cudaStreamSynchronize(s));
   const double rhsnorm = bits_to_double(H.hnorm[1]);

@@ -11,6 +11,8 @@ struct LevelData {
   double h = 1.0;
   std::shared_ptr<FabObj> phi, rhs;
   OpTable smooth, rr, prolong, zero;
+  // the stencil tables read neighbouring boxes directly (no ghost fill before them)
+  bool direct = false;
   // fused sweeps ping-pong between phi and phi2 (same layout)
   bool fused = false;
   std::shared_ptr<FabObj> phi2;
@@ -28,6 +30,7 @@ struct Hierarchy {
   std::vector<LevelData> L;
   std::shared_ptr<FabObj> phi0, rhs0;  // the caller's fabs (FP64)
   std::shared_ptr<FabObj> r0;          // mixed: FP64 residual stored by each norm check
+  bool direct0 = false;                // the norm check reads neighbouring boxes directly
   OpTable resid0, rhsabs0, scale0, correct0, zero0_64;
   DevBufP Mt, offr, offp, job;
   int N = 0;

@@ -36,7 +36,8 @@ class mg_options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("fixed_vcycles", ctypes.c_int),
-                ("h", ctypes.c_double), ("coarse_cells", ctypes.c_int)]
+                ("h", ctypes.c_double), ("coarse_cells", ctypes.c_int),
+                ("direct_reads", ctypes.c_int)]
 
 
 class mg_result(ctypes.Structure):
@@ -103,9 +104,9 @@ def make_bc(periodic=(1, 1, 1)):
 
 
 def make_options(nu1=2, nu2=2, max_iter=50, precision=MG_PREC_F64, smoother=MG_SMOOTH_AUTO,
-                 use_graph=1, fixed_vcycles=-1, h=0.0, coarse_cells=0):
+                 use_graph=1, fixed_vcycles=-1, h=0.0, coarse_cells=0, direct_reads=1):
     return mg_options(nu1, nu2, max_iter, precision, smoother, use_graph, fixed_vcycles, h,
-                      coarse_cells)
+                      coarse_cells, direct_reads)
 
 
 # ---- context -------------------------------------------------------------------------

@@ -198,3 +198,23 @@ def test_batch_coarse_cycle_kernel_bitwise(gctx, precision):
     assert out[0][1] == out[1][1] and all(s == mg.MG_OK for s, _ in out[0][1])
     for a, b in zip(out[0][0], out[1][0]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [mg.MG_PREC_F64, mg.MG_PREC_MIXED])
+def test_batch_direct_reads_bitwise(gctx, precision):
+    """Batched members reading neighbouring boxes directly (regular grids) or through filled
+    ghosts (uneven boxes) equal the batch that fills every level."""
+    out = []
+    for direct in (1, 0):
+        made = [_make(gctx, n, b, p, 600 + i) for i, (n, b, p) in enumerate(PROBLEMS)]
+        res = mg.mg_solve_batch(gctx, [m[1] for m in made], [m[2] for m in made],
+                                [mg.make_bc(p) for (_, _, p) in PROBLEMS], 1e-10,
+                                mg.make_options(precision=precision, direct_reads=direct))
+        out.append(([gu.fab_dense(gctx, m[2], m[0].shape) for m in made],
+                    [(r.status, r.vcycles) for r in res]))
+        for _, fr, fp in made:
+            mg.mg_fab_free(gctx, fr)
+            mg.mg_fab_free(gctx, fp)
+    assert out[0][1] == out[1][1] and all(s == mg.MG_OK for s, _ in out[0][1])
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)

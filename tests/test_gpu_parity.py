@@ -431,3 +431,41 @@ def test_coarse_cycle_kernel_bitwise(gctx, orc, ext, mb, periodic, precision, ce
                                     fixed_vcycles=2)
         assert vc == 2
         assert np.abs(c - o_phi).max() <= 1e-12 * np.abs(o_phi).max()
+
+
+# ---- stencils reading neighbouring boxes directly -----------------------------------------
+
+DIRECT_CASES = [
+    ((32, 32, 32), (16, 16, 16), (0, 0, 0), mg.MG_PREC_F64),
+    ((32, 32, 32), (8, 8, 8), (1, 1, 1), mg.MG_PREC_F64),
+    ((64, 32, 16), (16, 16, 16), (1, 0, 1), mg.MG_PREC_F64),
+    ((32, 32, 32), (32, 32, 32), (0, 1, 0), mg.MG_PREC_F64),     # one box: self images
+    ((32, 32, 32), (16, 32, 32), (1, 0, 0), mg.MG_PREC_F64),     # two boxes along x
+    ((48, 48, 48), (32, 32, 32), (0, 0, 0), mg.MG_PREC_F64),     # uneven boxes: fills
+    ((32, 32, 32), (16, 16, 16), (1, 0, 1), mg.MG_PREC_MIXED),
+]
+
+
+@pytest.mark.parametrize("ext,mb,periodic,precision", DIRECT_CASES)
+def test_direct_reads_equal_filled_ghosts(gctx, orc, ext, mb, periodic, precision):
+    """Solves whose stencils read neighbouring boxes (or periodic images, or the negated
+    boundary cell across Dirichlet faces) directly equal, bit for bit, solves that fill the
+    ghost layer first, with a non-zero initial guess."""
+    g = inputs.rng(49)
+    shape = tuple(reversed(ext))
+    rhs = g.standard_normal(shape)
+    if all(periodic):
+        rhs = inputs.remove_mean(rhs)
+    phi0 = 0.1 * g.standard_normal(shape)
+    # first use of a shape autotunes the fused FP32 sweep (extra launches): warm it up
+    _solve_with(gctx, ext, mb, periodic, rhs, phi0, mg.make_options(precision=precision))
+    out = []
+    for direct in (1, 0):
+        opt = mg.make_options(precision=precision, direct_reads=direct, coarse_cells=-1)
+        out.append(_solve_with(gctx, ext, mb, periodic, rhs, phi0, opt))
+    (a, ra, la), (b, rb, lb) = out
+    assert ra.status == rb.status == mg.MG_OK
+    assert ra.vcycles == rb.vcycles and ra.rel_resid == rb.rel_resid
+    assert np.array_equal(a, b)
+    if mb != (32, 32, 32) or ext != (48, 48, 48):
+        assert la < lb          # the fills are gone
