@@ -321,6 +321,55 @@ def test_full_size_dirichlet_256(gctx, orc):
     assert np.abs(phi - o_phi).max() <= 1e-12 * np.abs(o_phi).max()
 
 
+def test_full_size_mixed_512(gctx):
+    """The mixed-precision configuration at full size: 512^3 Dirichlet, 64 boxes of 128^3,
+    Gaussian blobs.  The answer meets 1e-10 (checked with an independent numpy residual) and
+    differs from the plain FP64 GPU answer by at most the bound two converged answers obey."""
+    n, tol = 512, 1e-10
+    rhs = inputs.gaussian_blobs(n, seed=5)
+    dom = (n - 1,) * 3
+    ba, _ = _ba(gctx, dom, (128, 128, 128))
+    fr = gu.dense_fab(gctx, ba, rhs, 1)
+    out = []
+    for prec in (mg.MG_PREC_MIXED, mg.MG_PREC_F64):
+        fp = mg.mg_fab_alloc(gctx, ba, 1, 2)
+        res = mg.mg_solve(gctx, fr, fp, mg.make_bc((0, 0, 0)), tol, mg.make_options(precision=prec))
+        assert res.status == mg.MG_OK and res.rel_resid <= tol
+        out.append(gu.fab_dense(gctx, fp, rhs.shape))
+        mg.mg_fab_free(gctx, fp)
+    mg.mg_fab_free(gctx, fr)
+    r = gu.residual_numpy(out[0], rhs, (0, 0, 0), 1.0 / n)
+    assert np.abs(r).max() <= 1.01 * tol * np.abs(rhs).max()
+    assert np.abs(out[0] - out[1]).max() <= 2 * 0.06 * tol * np.abs(rhs).max()
+
+
+def test_degenerate_domains(gctx, orc):
+    """One-cell domains (bottom only: the Dirichlet inverse, the periodic pseudo-inverse), a
+    domain with negative low corner, and flat boxes, all against the oracle."""
+    for per in [(0, 0, 0), (1, 1, 1), (1, 0, 1)]:
+        rhs = np.full((1, 1, 1), 0.0 if all(per) else 2.5)
+        phi, res = _solve_pair(gctx, orc, 1, (1, 1, 1), per, rhs)
+        o_phi, st, vc, _ = orc.solve(Z3, Z3, per, orc.chop(Z3, Z3, (1, 1, 1)), 1.0, rhs)
+        assert res.status == mg.MG_OK and res.vcycles == vc
+        assert np.array_equal(phi, o_phi) or np.abs(phi - o_phi).max() <= 1e-14
+    g = inputs.rng(50)
+    lo, hi = (-8, -16, 4), (7, 15, 19)
+    shape = tuple(h - l + 1 for l, h in zip(reversed(lo), reversed(hi)))
+    rhs = g.standard_normal(shape)
+    for mb in [(8, 8, 8), (16, 4, 16)]:
+        ba = mg.mg_box_array_create(gctx, lo, hi, mb)
+        fr, fp = gu.dense_fab(gctx, ba, rhs, 0), mg.mg_fab_alloc(gctx, ba, 1, 1)
+        res = mg.mg_solve(gctx, fr, fp, mg.make_bc((0, 1, 0)), 1e-10,
+                          mg.make_options(fixed_vcycles=3, h=1.0 / 16))
+        phi = gu.fab_dense(gctx, fp, rhs.shape)
+        o_phi, _, vc, _ = orc.solve(lo, hi, (0, 1, 0), orc.chop(lo, hi, mb), 1.0 / 16, rhs,
+                                    fixed_vcycles=3)
+        assert res.vcycles == vc == 3
+        assert np.abs(phi - o_phi).max() <= 1e-12 * np.abs(o_phi).max()
+        mg.mg_fab_free(gctx, fr)
+        mg.mg_fab_free(gctx, fp)
+
+
 # ---- fused red + black sweep (TMA-staged z-slabs) ---------------------------------------
 
 FUSED_CASES = [((63, 63, 63), (64, 64, 64)), ((47, 37, 21), (24, 19, 11)), ((15, 15, 15), (4, 4, 4)),
