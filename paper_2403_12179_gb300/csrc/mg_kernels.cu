@@ -88,13 +88,15 @@ __device__ __forceinline__ int find_seg(const Seg* __restrict__ segs, int n, lon
   return lo;
 }
 
-// Block k owns launch rows [k*per, (k+1)*per); warp w of the block takes rows begin+w,
-// +kWarps, ...  f(row, row-within-box, slot) is called once per row with all 32 lanes active.
-template <class F>
+// Block k owns launch rows [k*per, (k+1)*per); with HW = 1 warp w of the block takes rows
+// begin+w, +kWarps, ...; with HW = 2 each half-warp takes its own row (begin + 2w + half,
+// step 2 kWarps).  f(row, row-within-box, slot) is called once per row with all lanes of the
+// (half-)warp active.
+template <int HW = 1, class F>
 __device__ __forceinline__ void for_rows(const SegList& L, long long nrows, long long per, F&& f) {
   long long begin = (long long)blockIdx.x * per;
   long long end = begin + per < nrows ? begin + per : nrows;
-  long long r = begin + (threadIdx.x >> 5);
+  long long r = begin + (long long)(threadIdx.x >> 5) * HW + (HW == 2 ? ((threadIdx.x >> 4) & 1) : 0);
   if (r >= end) return;
   int si = 0;
   Seg S = L.one;
@@ -103,7 +105,7 @@ __device__ __forceinline__ void for_rows(const SegList& L, long long nrows, long
     S = L.segs[si];
   }
   int b = find_box(S.rows, S.nbox, r - S.row_begin);
-  for (; r < end; r += kWarps) {
+  for (; r < end; r += kWarps * HW) {
     if (L.n > 1) {
       bool moved = false;
       while (si + 1 < L.n && L.segs[si + 1].row_begin <= r) {
@@ -269,39 +271,6 @@ __global__ void __launch_bounds__(256) k_copy_tags(TagList L, long long nchunks,
 }
 
 // ---------------------------------------------------------------------------------------
-// Red-black Gauss-Seidel half-sweep: cells with (i+j+k) mod 2 == color (global indices)
-// take phi = (s - h^2 rhs) / 6.  Lane l of a warp updates cells par + 2l (+64 k) of a line.
-// DIRECT: box-face neighbours through DRow::nbd / nbf (rows without that information read
-// their ghost cells); else ghost cells, through plain offsets.
-template <class T, bool DIRECT>
-__global__ void __launch_bounds__(kThreads, DIRECT ? 4 : 6) k_rbgs_half(SegList L, long long nrows, long long per,
-                                                        int color) {
-  const int lane = threadIdx.x & 31;
-  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
-    const int n0 = R.n[0], n1 = R.n[1];
-    const int y = (int)(lr % n1), z = (int)(lr / n1);
-    T* phi = line<T>(R.v[0], y, z);
-    const T* rhs = line<T>(R.v[1], y, z);
-    const T h2 = (T)R.h2;
-    const int par = (color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1;
-    if constexpr (DIRECT) {
-      const Nbr<T> nb = nbr_rows<T>(R, phi, y, z);
-      if (nb.neg == 0) {
-        for (int x = par + 2 * lane; x < n0; x += 64)
-          phi[x] = gs_update(nbr_sum_rows<false>(phi, x, n0, nb), rhs[x], h2);
-      } else {
-        for (int x = par + 2 * lane; x < n0; x += 64)
-          phi[x] = gs_update(nbr_sum_rows<true>(phi, x, n0, nb), rhs[x], h2);
-      }
-    } else {
-      const int pitch = R.v[0].pitch;
-      const long long plane = R.v[0].plane;
-      for (int x = par + 2 * lane; x < n0; x += 64)
-        phi[x] = gs_update(nbr_sum(phi + x, pitch, plane), rhs[x], h2);
-    }
-  });
-}
-
 // Flush per-warp maxima: each warp stores (slot, max); thread 0 merges equal slots.
 __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
                                                 unsigned long long* norms) {
@@ -327,11 +296,78 @@ __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
   }
 }
 
+// Red-black Gauss-Seidel half-sweep: cells with (i+j+k) mod 2 == color (global indices)
+// take phi = (s - h^2 rhs) / 6.  Lane l of a warp updates cells par + 2l (+64 k) of a line.
+// DIRECT: box-face neighbours through DRow::nbd / nbf (rows without that information read
+// their ghost cells); else ghost cells, through plain offsets.
+// norms != null (single-segment launches, DIRECT only): also the max-norm of the residual of
+// every updated cell just after its update, into norms[slot + solve].  The neighbour sum of
+// the update serves, since the other colour's cells are unchanged by this half-sweep --
+// except where a read is the cell's own value negated (a Dirichlet face): those cells sum
+// again, reading their new value.  (With an odd periodic extent an image could be the cell's
+// own colour; callers use this on even periodic extents only.)
+template <class T, bool DIRECT>
+__global__ void __launch_bounds__(kThreads, 4) k_rbgs_half(SegList L, long long nrows, long long per,
+                                                        int color, unsigned long long* norms) {
+  // Half a warp per row; a lane updates cells x and x + 32 of a pair step together (both red:
+  // their neighbours are black and unchanged, so both loads go first -- two independent FP64
+  // chains per lane).
+  const int sub = threadIdx.x & 15;
+  unsigned long long mx = 0;
+  int cur = -1;
+  for_rows<2>(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    T* phi = line<T>(R.v[0], y, z);
+    const T* rhs = line<T>(R.v[1], y, z);
+    const T h2 = (T)R.h2, ih2 = (T)R.ih2;
+    const int par = (color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1;
+    cur = slot + R.solve;
+    auto norm = [&](T s, T u, T r) {
+      const unsigned long long k = Ar<T>::abskey(residual_of(s, u, r, ih2));
+      mx = k > mx ? k : mx;
+    };
+    auto sweep = [&](auto&& sum, auto&& resum) {
+      for (int x = par + 2 * sub; x < n0; x += 64) {
+        const int x2 = x + 32;
+        const bool two = x2 < n0;
+        const T s1 = sum(x);
+        const T s2 = two ? sum(x2) : T(0);
+        const T r1 = rhs[x];
+        const T r2 = two ? rhs[x2] : T(0);
+        const T u1 = gs_update(s1, r1, h2);
+        phi[x] = u1;
+        if (norms) norm(resum(x, s1), u1, r1);
+        if (two) {
+          const T u2 = gs_update(s2, r2, h2);
+          phi[x2] = u2;
+          if (norms) norm(resum(x2, s2), u2, r2);
+        }
+      }
+    };
+    if constexpr (DIRECT) {
+      const Nbr<T> nb = nbr_rows<T>(R, phi, y, z);
+      // cells with a negated read of their own value sum again after their update
+      auto resum = [&](int x, T s) {
+        const bool own = (nb.neg & 60u) || (x == 0 && (nb.neg & 1u)) || (x == n0 - 1 && (nb.neg & 2u));
+        return own ? nbr_sum_rows<true>(phi, x, n0, nb) : s;
+      };
+      if (nb.neg == 0) sweep([&](int x) { return nbr_sum_rows<false>(phi, x, n0, nb); }, resum);
+      else sweep([&](int x) { return nbr_sum_rows<true>(phi, x, n0, nb); }, resum);
+    } else {
+      const int pitch = R.v[0].pitch;
+      const long long plane = R.v[0].plane;
+      sweep([&](int x) { return nbr_sum(phi + x, pitch, plane); }, [](int, T s) { return s; });
+    }
+  });
+  if (norms) flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
+}
+
 // Residual r = rhs - (s - 6 phi) / h^2, optionally stored, with a fused max-norm into
 // norms[slot + solve].
 template <class T, bool DIRECT>
 __global__ void __launch_bounds__(kThreads, DIRECT ? 4 : 6) k_residual(SegList L, long long nrows, long long per,
-                                                       unsigned long long* norms) {
+                                                       unsigned long long* norms, int color) {
   const int lane = threadIdx.x & 31;
   unsigned long long mx = 0;
   int cur = -1;
@@ -358,14 +394,17 @@ __global__ void __launch_bounds__(kThreads, DIRECT ? 4 : 6) k_residual(SegList L
       unsigned long long k = Ar<T>::abskey(v);
       mx = k > mx ? k : mx;
     };
+    // color < 0: every cell; else the cells of that colour only
+    const int x0 = color < 0 ? lane : ((color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1) + 2 * lane;
+    const int dx = color < 0 ? 32 : 64;
     if constexpr (DIRECT) {
       if (nb.neg == 0) {
-        for (int x = lane; x < n0; x += 32) cell(x, nbr_sum_rows<false>(phi, x, n0, nb));
+        for (int x = x0; x < n0; x += dx) cell(x, nbr_sum_rows<false>(phi, x, n0, nb));
       } else {
-        for (int x = lane; x < n0; x += 32) cell(x, nbr_sum_rows<true>(phi, x, n0, nb));
+        for (int x = x0; x < n0; x += dx) cell(x, nbr_sum_rows<true>(phi, x, n0, nb));
       }
     } else {
-      for (int x = lane; x < n0; x += 32) cell(x, nbr_sum(phi + x, R.v[0].pitch, R.v[0].plane));
+      for (int x = x0; x < n0; x += dx) cell(x, nbr_sum(phi + x, R.v[0].pitch, R.v[0].plane));
     }
   });
   if (norms) flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
@@ -661,19 +700,20 @@ cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int n
 }
 
 cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int color, cudaStream_t s,
-                               bool direct) {
+                               bool direct, unsigned long long* norms) {
   if (nrows <= 0) return cudaSuccess;
+  if (norms && (L.n != 1 || !direct)) return cudaErrorInvalidValue;
   Grid g = row_grid(nrows, 16);
-  GB_DISPATCH_D(dt, direct, k_rbgs_half, g.blocks, kThreads, 0, s, L, nrows, g.per, color);
+  GB_DISPATCH_D(dt, direct, k_rbgs_half, g.blocks, kThreads, 0, s, L, nrows, g.per, color, norms);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
-                              cudaStream_t s, bool direct) {
+                              cudaStream_t s, bool direct, int color) {
   if (nrows <= 0) return cudaSuccess;
   Grid g = row_grid(nrows, 16);
-  GB_DISPATCH_D(dt, direct, k_residual, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
+  GB_DISPATCH_D(dt, direct, k_residual, g.blocks, kThreads, 0, s, L, nrows, g.per, norms, color);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -733,13 +773,13 @@ cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsign
 // ---- single-table launchers (one segment) ------------------------------------------------
 
 cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
-                             cudaStream_t s, bool direct) {
-  return launch_rbgs_half_l(dt, one_seg(rows, nbox), nrows, color, s, direct);
+                             cudaStream_t s, bool direct, unsigned long long* norms) {
+  return launch_rbgs_half_l(dt, one_seg(rows, nbox), nrows, color, s, direct, norms);
 }
 
 cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
-                            unsigned long long* norms, cudaStream_t s, bool direct) {
-  return launch_residual_l(dt, one_seg(rows, nbox), nrows, norms, s, direct);
+                            unsigned long long* norms, cudaStream_t s, bool direct, int color) {
+  return launch_residual_l(dt, one_seg(rows, nbox), nrows, norms, s, direct, color);
 }
 
 cudaError_t launch_residual_restrict(int dt, const DRow* rows, int nbox, long long nrows,

@@ -170,14 +170,19 @@ cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int n
 // Stencil launchers: with direct = true the kernel reads box-face neighbours through
 // DRow::nbd / nbf (rows whose nbd / nbf are zero read their ghost cells); with false it reads
 // the ghost cells (filled beforehand) through plain offsets.
-// v[0] = phi, v[1] = rhs.
+// v[0] = phi, v[1] = rhs.  norms != null (direct, single-table launches only): also atomicMax
+// of |residual| of every updated cell after its update into norms[solve] (valid when the
+// box array's periodic extents are even).
 cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
-                             cudaStream_t s, bool direct = false);
+                             cudaStream_t s, bool direct = false,
+                             unsigned long long* norms = nullptr);
 
 // v[0] = phi, v[1] = rhs, v[2] = r (p == null: not stored).  norms[solve] receives
-// atomicMax of the bit pattern of |r| (NaN propagates as the largest pattern).
+// atomicMax of the bit pattern of |r| (NaN propagates as the largest pattern).  color < 0:
+// every cell; 0 / 1: the cells of that colour only.
 cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
-                            unsigned long long* norms, cudaStream_t s, bool direct = false);
+                            unsigned long long* norms, cudaStream_t s, bool direct = false,
+                            int color = -1);
 
 // Rows are coarse x-lines.  v[0] = phi, v[1] = rhs (fine); c[0] = coarse rhs,
 // c[1] = coarse phi (p == null: not zeroed).
@@ -241,9 +246,9 @@ cudaError_t launch_correct_add(const DRow* rows, int nbox, long long nrows,
 // the totals over all segments.
 cudaError_t launch_copy_tags_l(int dt, const TagList& L, long long nchunks, int ncomp, cudaStream_t s);
 cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int color, cudaStream_t s,
-                               bool direct = false);
+                               bool direct = false, unsigned long long* norms = nullptr);
 cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
-                              cudaStream_t s, bool direct = false);
+                              cudaStream_t s, bool direct = false, int color = -1);
 cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s,
                                        bool direct = false);
 cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cudaStream_t s);

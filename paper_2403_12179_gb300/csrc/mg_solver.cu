@@ -297,7 +297,10 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
 
 namespace {
 
-void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s) {
+// last_norm != null: the final (black) half-sweep also accumulates the residual max-norm of
+// the cells it updates there (the caller adds the red cells).
+void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s,
+            unsigned long long* last_norm = nullptr) {
   int k = 0;
   if (D.fused) {
     // pairs of fused sweeps: phi -> phi2 -> phi
@@ -311,12 +314,13 @@ void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s) {
   for (; k < sweeps; ++k)
     for (int color = 0; color < 2; ++color) {
       if (!D.direct) launch_fill(c, *D.phi, &H.bc, s, 1);  // the half-sweep reads one layer
+      const bool last = k + 1 == sweeps && color == 1;
       MG_CK(launch_rbgs_half(H.dt, D.smooth.rows(), D.smooth.nbox, D.smooth.nrows, color, s,
-                             D.direct));
+                             D.direct, last ? last_norm : nullptr));
     }
 }
 
-void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s) {
+void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s, unsigned long long* norm0 = nullptr) {
   const int nl = (int)H.L.size();
   const int top = H.lc < nl ? H.lc : nl - 1;  // levels below `top` run stage by stage
   for (int l = 0; l < top; ++l) {
@@ -331,7 +335,7 @@ void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s) {
   for (int l = top - 1; l >= 0; --l) {
     LevelData& D = H.L[l];
     MG_CK(launch_prolong_add(H.dt, D.prolong.rows(), D.prolong.nbox, D.prolong.nrows, s));
-    smooth(c, H, D, H.p.nu2, s);
+    smooth(c, H, D, H.p.nu2, s, l == 0 ? norm0 : nullptr);
   }
 }
 
@@ -341,12 +345,25 @@ void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
   unsigned long long* dn = (unsigned long long*)H.dnorm->p;
   if (H.mixed)  // the FP32 right-hand side from the residual of the last norm check; e = 0
     MG_CK(launch_scale_residual_f32(H.scale0.rows(), H.scale0.nbox, H.scale0.nrows, dn, s));
-  enqueue_vcycle(c, H, s);
+  // FP64 with half-sweeps on the finest level: the cycle's last (black) half-sweep there
+  // takes the residual norm of the cells it updates, and only the red cells need a residual
+  // pass; the values are those of a full residual pass
+  bool split_norm = !H.mixed && H.lc > 0 && H.p.nu2 >= 1 && !H.L[0].fused && H.direct0 &&
+                    H.L[0].direct;
+  {
+    int per[3];
+    bc_code(&H.bc, per);
+    for (int d = 0; d < 3; ++d)  // an odd periodic extent maps a ghost onto its own colour
+      if (per[d] && (H.L[0].bao->ba.dom.len(d) & 1)) split_norm = false;
+  }
+  if (split_norm) MG_CK(cudaMemsetAsync(dn, 0, 8, s));
+  enqueue_vcycle(c, H, s, split_norm ? dn : nullptr);
   if (H.mixed)
     MG_CK(launch_correct_add(H.correct0.rows(), H.correct0.nbox, H.correct0.nrows, dn, s));
-  MG_CK(cudaMemsetAsync(dn, 0, 8, s));
+  if (!split_norm) MG_CK(cudaMemsetAsync(dn, 0, 8, s));
   if (!H.direct0) launch_fill(c, *H.phi0, &H.bc, s, 1);
-  MG_CK(launch_residual(DT_F64, H.resid0.rows(), H.resid0.nbox, H.resid0.nrows, dn, s, H.direct0));
+  MG_CK(launch_residual(DT_F64, H.resid0.rows(), H.resid0.nbox, H.resid0.nrows, dn, s, H.direct0,
+                        split_norm ? 0 : -1));
   MG_CK(cudaMemcpyAsync(H.hnorm, dn, 16, cudaMemcpyDeviceToHost, s));
 }
 

@@ -518,3 +518,24 @@ def test_direct_reads_equal_filled_ghosts(gctx, orc, ext, mb, periodic, precisio
     assert np.array_equal(a, b)
     if mb != (32, 32, 32) or ext != (48, 48, 48):
         assert la < lb          # the fills are gone
+
+
+@pytest.mark.parametrize("periodic,direct", [((0, 0, 0), 1), ((1, 0, 1), 1), ((0, 0, 0), 0)])
+def test_solve_norm_equals_full_residual_norm(gctx, periodic, direct):
+    """The norm a solve reports after each V-cycle -- its last black half-sweep takes the
+    black cells' residuals, a second pass the red ones -- equals the max-norm of a full
+    residual pass over the final iterate."""
+    n, mb = 32, (16, 16, 16)
+    rhs = inputs.rng(51).standard_normal((n, n, n))
+    ba, _ = _ba(gctx, (n - 1,) * 3, mb)
+    fr, fp = gu.dense_fab(gctx, ba, rhs, 0), mg.mg_fab_alloc(gctx, ba, 1, 1)
+    bc = mg.make_bc(periodic)
+    for k in (1, 3):
+        mg.mg_fab_set_val(gctx, fp, 0.0, True)
+        res = mg.mg_solve(gctx, fr, fp, bc, 1e-10,
+                          mg.make_options(fixed_vcycles=k, direct_reads=direct, coarse_cells=-1))
+        mg.mg_fill_boundary(gctx, fp, bc)
+        full = mg.mg_residual(gctx, fp, fr, 0, 1.0 / n)
+        assert res.vcycles == k and res.rel_resid == full / float(np.abs(rhs).max())
+    mg.mg_fab_free(gctx, fr)
+    mg.mg_fab_free(gctx, fp)
