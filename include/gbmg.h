@@ -57,6 +57,7 @@ enum { MG_F64 = 0, MG_F32 = 1 };                    /* fab element types */
 enum { MG_BC_PERIODIC = 0, MG_BC_DIRICHLET0 = 1 };  /* face kinds */
 enum { MG_PREC_F64 = 0, MG_PREC_MIXED = 1 };        /* solver precision */
 enum { MG_SMOOTH_AUTO = 0, MG_SMOOTH_HALF = 1, MG_SMOOTH_FUSED = 2 };
+enum { MG_SMOOTH_DIRECT_READS = 4 };  /* flag for mg_smooth's color (see there) */
 
 /* Boundary conditions: kind[d][0] / kind[d][1] for the low / high face of dimension d.
  * A periodic dimension must be periodic on both faces.  MG_BC_DIRICHLET0 is homogeneous
@@ -224,6 +225,9 @@ int mg_fill_boundary_unfused(mg_ctx_t ctx, mg_fab_t fab, const mg_bc* bc, void* 
 /* Red-black Gauss-Seidel on 1-component fabs of one box array with cell size h.
  * color 0 / 1: one half-sweep of that colour ((i+j+k) mod 2 on global indices), using
  *   phi's ghosts as they are (fill them first); rhs needs no ghosts.
+ * color 0 / 1 | MG_SMOOTH_DIRECT_READS: the same half-sweep reading each box's neighbours
+ *   (periodic images; the negated boundary cell across a Dirichlet face) directly instead of
+ *   ghost cells, as the solver does; boxes must form a regular grid (else MG_EINVAL).
  * color 2: one full sweep, equal to fill, red, fill, black; with phi nghost >= 2 and rhs
  *   nghost >= 1 it runs as one fused kernel after one fill of each.
  * Update: phi_c = (s - h^2 rhs_c) / 6, s = x- + x+ + y- + y+ + z- + z+ (in that order). */
@@ -329,6 +333,15 @@ int mg_server_stats_get(mg_ctx_t ctx, mg_server_stats* out);
  * *res filled when done (the ticket is then released), MG_PENDING if not done in time,
  * MG_EINVAL for an unknown ticket. */
 int mg_poll(mg_ctx_t ctx, mg_ticket_t ticket, int timeout_ms, mg_result* res);
+
+/* ---- instrumentation (no counterpart in the paper) ---------------------------------- */
+
+/* Device time of the finest-level red-black half-sweep inside mg_solve: while enabled, each
+ * V-cycle of an FP64 solve (finest level smoothed by half-sweeps) records a CUDA event pair on
+ * the solve stream around its first finest-level half-sweep (captured into the step graph).
+ * Returns in *total_ms / *launches (either may be NULL) the sum and count accumulated since
+ * the previous call, resets them, and sets the mode for later solves. */
+int mg_sweep_timing(mg_ctx_t ctx, int enable, double* total_ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

@@ -188,18 +188,19 @@ __device__ __forceinline__ Nbr<T> nbr_rows(const DRow& R, const T* row, int y, i
   return b;
 }
 
-// The six-neighbour sum of cell x of `row` (order x-, x+, y-, y+, z-, z+) through Nbr.
-// NEG = false: the row has no negated reads (interior and periodic faces: the common case,
-// decided per row so that a warp takes one branch).
-template <bool NEG, class T>
+// The six-neighbour sum of cell x of `row` (order x-, x+, y-, y+, z-, z+) through Nbr.  The
+// x-face negations (whole boxes) apply to the end cells only; NEGYZ: the row also has negated
+// y / z reads (its box's face rows at a Dirichlet face -- decided per row, so a warp takes
+// one branch).
+template <bool NEGYZ, class T>
 __device__ __forceinline__ T nbr_sum_rows(const T* row, int x, int nx, const Nbr<T>& b) {
   const bool e0 = x == 0, e1 = x == nx - 1;
   T xm = row[x - 1 + (e0 ? b.dxm : 0)];
   T xp = row[x + 1 + (e1 ? b.dxp : 0)];
+  if (e0) xm = xsign(xm, b.neg & 1u);
+  if (e1) xp = xsign(xp, (b.neg >> 1) & 1u);
   T ym = b.ym[x], yp = b.yp[x], zm = b.zm[x], zp = b.zp[x];
-  if (NEG) {
-    xm = xsign(xm, e0 ? b.neg & 1u : 0u);
-    xp = xsign(xp, e1 ? (b.neg >> 1) & 1u : 0u);
+  if (NEGYZ) {
     ym = xsign(ym, (b.neg >> 2) & 1u);
     yp = xsign(yp, (b.neg >> 3) & 1u);
     zm = xsign(zm, (b.neg >> 4) & 1u);
@@ -213,6 +214,7 @@ __device__ __forceinline__ T nbr_sum_rows(const T* row, int x, int nx, const Nbr
   return s;
 }
 
+// ---------------------------------------------------------------------------------------
 // Copy tags (ghost fill).  One warp per chunk of whole x-rows of one tag (tag_chunk_rows).
 // Segments = fabs.  Sources are valid cells and destinations ghost cells, never the same
 // memory within a launch, so sources are read through the read-only path.
@@ -306,7 +308,7 @@ __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
 // except where a read is the cell's own value negated (a Dirichlet face): those cells sum
 // again, reading their new value.  (With an odd periodic extent an image could be the cell's
 // own colour; callers use this on even periodic extents only.)
-template <class T, bool DIRECT>
+template <class T, bool DIRECT, bool NORM = false>
 __global__ void __launch_bounds__(kThreads, 4) k_rbgs_half(SegList L, long long nrows, long long per,
                                                         int color, unsigned long long* norms) {
   // Half a warp per row; a lane updates cells x and x + 32 of a pair step together (both red:
@@ -337,11 +339,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_rbgs_half(SegList L, long long 
         const T r2 = two ? rhs[x2] : T(0);
         const T u1 = gs_update(s1, r1, h2);
         phi[x] = u1;
-        if (norms) norm(resum(x, s1), u1, r1);
+        if (NORM) norm(resum(x, s1), u1, r1);
         if (two) {
           const T u2 = gs_update(s2, r2, h2);
           phi[x2] = u2;
-          if (norms) norm(resum(x2, s2), u2, r2);
+          if (NORM) norm(resum(x2, s2), u2, r2);
         }
       }
     };
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_rbgs_half(SegList L, long long 
         const bool own = (nb.neg & 60u) || (x == 0 && (nb.neg & 1u)) || (x == n0 - 1 && (nb.neg & 2u));
         return own ? nbr_sum_rows<true>(phi, x, n0, nb) : s;
       };
-      if (nb.neg == 0) sweep([&](int x) { return nbr_sum_rows<false>(phi, x, n0, nb); }, resum);
+      if ((nb.neg & 60u) == 0) sweep([&](int x) { return nbr_sum_rows<false>(phi, x, n0, nb); }, resum);
       else sweep([&](int x) { return nbr_sum_rows<true>(phi, x, n0, nb); }, resum);
     } else {
       const int pitch = R.v[0].pitch;
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_rbgs_half(SegList L, long long 
       sweep([&](int x) { return nbr_sum(phi + x, pitch, plane); }, [](int, T s) { return s; });
     }
   });
-  if (norms) flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
+  if (NORM) flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
 }
 
 // Residual r = rhs - (s - 6 phi) / h^2, optionally stored, with a fused max-norm into
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, DIRECT ? 4 : 6) k_residual(SegList L
     const int x0 = color < 0 ? lane : ((color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1) + 2 * lane;
     const int dx = color < 0 ? 32 : 64;
     if constexpr (DIRECT) {
-      if (nb.neg == 0) {
+      if ((nb.neg & 60u) == 0) {
         for (int x = x0; x < n0; x += dx) cell(x, nbr_sum_rows<false>(phi, x, n0, nb));
       } else {
         for (int x = x0; x < n0; x += dx) cell(x, nbr_sum_rows<true>(phi, x, n0, nb));
@@ -436,8 +438,8 @@ __global__ void __launch_bounds__(kThreads) k_residual_restrict(SegList L, long 
           for (int i = 0; i < 2; ++i) {
             const T* q = line<T>(vr, 2 * Y + j, 2 * Z + k) + 2 * X + i;
             T s = !DIRECT ? nbr_sum(row + 2 * X + i, vp.pitch, vp.plane)
-                          : nb.neg ? nbr_sum_rows<true>(row, 2 * X + i, n0, nb)
-                                   : nbr_sum_rows<false>(row, 2 * X + i, n0, nb);
+                          : (nb.neg & 60u) ? nbr_sum_rows<true>(row, 2 * X + i, n0, nb)
+                                           : nbr_sum_rows<false>(row, 2 * X + i, n0, nb);
             T v = residual_of(s, row[2 * X + i], q[0], ih2);
             acc = (i | j | k) ? Ar<T>::add(acc, v) : v;
           }
@@ -704,7 +706,12 @@ cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int co
   if (nrows <= 0) return cudaSuccess;
   if (norms && (L.n != 1 || !direct)) return cudaErrorInvalidValue;
   Grid g = row_grid(nrows, 16);
-  GB_DISPATCH_D(dt, direct, k_rbgs_half, g.blocks, kThreads, 0, s, L, nrows, g.per, color, norms);
+  if (norms) {
+    if (dt == DT_F64) k_rbgs_half<double, true, true><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+    else k_rbgs_half<float, true, true><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+  } else {
+    GB_DISPATCH_D(dt, direct, k_rbgs_half, g.blocks, kThreads, 0, s, L, nrows, g.per, color, norms);
+  }
   count_launches(1);
   return cudaGetLastError();
 }

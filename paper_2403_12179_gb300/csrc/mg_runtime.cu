@@ -1053,7 +1053,29 @@ int mg_smooth(mg_ctx_t h, mg_fab_t phi, mg_fab_t rhs, const mg_bc* bc, double hh
     auto fr = c->get_fab(rhs);
     same_shape(*fp, *fr, "mg_smooth");
     if (fp->lay.g < 1) fail(MG_EINVAL, "phi needs at least one ghost cell");
-    if (color < 0 || color > 2) fail(MG_EINVAL, "color must be 0, 1 or 2");
+    if ((color & ~MG_SMOOTH_DIRECT_READS) == 0 || (color & ~MG_SMOOTH_DIRECT_READS) == 1) {
+      if (color & MG_SMOOTH_DIRECT_READS) {  // one half-sweep reading neighbouring boxes
+        int per[3];
+        const int code = bc_code(bc, per);
+        cudaStream_t s = S(stream);
+        double hv = default_h(*fp, hh);
+        const std::string op = "smooth_direct" + std::to_string(code);
+        const OpTable& t = op_table(*c, op.c_str(), {phi, rhs}, hv, [&] {
+          FaceReads faces = direct_neighbours(*fp, per);
+          if (!faces.ok()) fail(MG_EINVAL, "direct reads need boxes on a regular grid");
+          OpTable tt = make_table(*c, fp->ba->ba, 0, hv, 0, [&](int b, DRow& R) {
+            R.v[0] = fp->view(b);
+            R.v[1] = fr->view(b);
+            faces.apply(b, R);
+          }, c->stream);
+          tt.direct = true;
+          return tt;
+        });
+        MG_CK(launch_rbgs_half(fp->dtype, t.rows(), t.nbox, t.nrows, color & 1, s, true));
+        return MG_OK;
+      }
+    }
+    if (color < 0 || color > 2) fail(MG_EINVAL, "color must be 0, 1 or 2 (0 / 1 may add MG_SMOOTH_DIRECT_READS)");
     cudaStream_t s = S(stream);
     double hv = default_h(*fp, hh);
     const OpTable& t = op_table(*c, "smooth", {phi, rhs}, hv, [&] {

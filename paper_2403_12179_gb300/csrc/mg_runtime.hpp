@@ -143,6 +143,12 @@ struct FusedCfg {
 };
 
 struct Ctx {
+  // Timing of the finest-level half-sweep inside solves (one CUDA event pair around the
+  // first such launch of every V-cycle, recorded on the solve stream; captured into the
+  // step graph when enabled).
+  bool sweep_timing = false;
+  double sweep_ms = 0.0;
+  long long sweep_n = 0;
   int device = -1;
   cudaStream_t stream = nullptr;   // context stream (solves)
   cudaStream_t own_stream = nullptr;

@@ -300,7 +300,7 @@ namespace {
 // last_norm != null: the final (black) half-sweep also accumulates the residual max-norm of
 // the cells it updates there (the caller adds the red cells).
 void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s,
-            unsigned long long* last_norm = nullptr) {
+            unsigned long long* last_norm = nullptr, bool time_first = false) {
   int k = 0;
   if (D.fused) {
     // pairs of fused sweeps: phi -> phi2 -> phi
@@ -315,8 +315,12 @@ void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s,
     for (int color = 0; color < 2; ++color) {
       if (!D.direct) launch_fill(c, *D.phi, &H.bc, s, 1);  // the half-sweep reads one layer
       const bool last = k + 1 == sweeps && color == 1;
+      const bool timed = time_first && k == 0 && color == 0;
+      // (external records: captured into the step graph as event-record nodes)
+      if (timed) MG_CK(cudaEventRecordWithFlags(H.sweep_ev[0], s, cudaEventRecordExternal));
       MG_CK(launch_rbgs_half(H.dt, D.smooth.rows(), D.smooth.nbox, D.smooth.nrows, color, s,
                              D.direct, last ? last_norm : nullptr));
+      if (timed) MG_CK(cudaEventRecordWithFlags(H.sweep_ev[1], s, cudaEventRecordExternal));
     }
 }
 
@@ -326,7 +330,7 @@ void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s, unsigned long long* no
   for (int l = 0; l < top; ++l) {
     LevelData& D = H.L[l];
     if (D.fused) launch_fill(c, *D.rhs, &H.bc, s, 1);  // rhs ghosts for the redundant ring
-    smooth(c, H, D, H.p.nu1, s);
+    smooth(c, H, D, H.p.nu1, s, nullptr, l == 0 && H.graph_timed);
     if (!D.direct) launch_fill(c, *D.phi, &H.bc, s, 1);
     MG_CK(launch_residual_restrict(H.dt, D.rr.rows(), D.rr.nbox, D.rr.nrows, s, D.direct));
   }
@@ -369,6 +373,13 @@ void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
 
 void run_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
   bool graph = H.p.use_graph && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+  if (c.sweep_timing && !H.sweep_ev[0])
+    for (cudaEvent_t& e : H.sweep_ev) MG_CK(cudaEventCreate(&e));
+  if (H.step_graph && H.graph_timed != c.sweep_timing) {  // timing switched: capture again
+    cudaGraphExecDestroy(H.step_graph);
+    H.step_graph = nullptr;
+  }
+  H.graph_timed = c.sweep_timing;
   if (graph && H.step_graph && H.graph_stream != s) {
     cudaGraphExecDestroy(H.step_graph);
     H.step_graph = nullptr;
@@ -469,6 +480,13 @@ int solve(Ctx& c, int64_t rhs_id, int64_t phi_id, const mg_bc* bc, double tol,
       run_step(c, H, s);
       MG_CK(cudaStreamSynchronize(s));
       rn = bits_to_double(H.hnorm[0]);
+      if (H.graph_timed && H.lc > 0 && !H.L[0].fused) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, H.sweep_ev[0], H.sweep_ev[1]) == cudaSuccess) {
+          c.sweep_ms += ms;
+          c.sweep_n += 1;
+        }
+      }
       ++it;
     }
   }
@@ -487,6 +505,19 @@ int solve(Ctx& c, int64_t rhs_id, int64_t phi_id, const mg_bc* bc, double tol,
 using namespace gbmg;
 
 extern "C" {
+
+int mg_sweep_timing(mg_ctx_t h, int enable, double* total_ms, int64_t* launches) {
+  return guard([&] {
+    Ctx* c = (Ctx*)h;
+    if (!c) fail(MG_EINVAL, "ctx is NULL");
+    if (total_ms) *total_ms = c->sweep_ms;
+    if (launches) *launches = c->sweep_n;
+    c->sweep_ms = 0.0;
+    c->sweep_n = 0;
+    c->sweep_timing = enable != 0;
+    return MG_OK;
+  });
+}
 
 int mg_solve(mg_ctx_t h, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, double tol,
              const mg_options* opt, mg_result* res) {

@@ -45,9 +45,13 @@ struct Hierarchy {
   cudaGraphExec_t step_graph = nullptr;
   cudaStream_t graph_stream = nullptr;
   long long graph_kernels = 0;
+  bool graph_timed = false;                  // the step graph records sweep_ev
+  cudaEvent_t sweep_ev[2] = {nullptr, nullptr};
   ~Hierarchy() {
     if (step_graph) cudaGraphExecDestroy(step_graph);
     if (hnorm) cudaFreeHost(hnorm);
+    for (cudaEvent_t e : sweep_ev)
+      if (e) cudaEventDestroy(e);
   }
 };
 

@@ -24,6 +24,7 @@ MG_F64, MG_F32 = 0, 1
 MG_BC_PERIODIC, MG_BC_DIRICHLET0 = 0, 1
 MG_PREC_F64, MG_PREC_MIXED = 0, 1
 MG_SMOOTH_AUTO, MG_SMOOTH_HALF, MG_SMOOTH_FUSED = 0, 1, 2
+MG_SMOOTH_DIRECT_READS = 4
 
 _c_int3 = ctypes.c_int * 3
 
@@ -418,3 +419,12 @@ class BoxView:
     def __cuda_array_interface__(self):
         return {"shape": self.shape, "typestr": self.typestr, "data": (self.ptr, False),
                 "strides": self.strides, "version": 3}
+
+
+def mg_sweep_timing(ctx, enable):
+    """Enable / disable timing of the finest-level half-sweep inside solves; returns
+    (total_ms, launches) accumulated since the previous call."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _ck(lib().mg_sweep_timing(ctx, ctypes.c_int(1 if enable else 0), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value

@@ -539,3 +539,43 @@ def test_solve_norm_equals_full_residual_norm(gctx, periodic, direct):
         assert res.vcycles == k and res.rel_resid == full / float(np.abs(rhs).max())
     mg.mg_fab_free(gctx, fr)
     mg.mg_fab_free(gctx, fp)
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (0, 1, 1)])
+def test_smooth_direct_reads_equals_filled(gctx, periodic):
+    """mg_smooth with MG_SMOOTH_DIRECT_READS (neighbour boxes read directly, ghost cells
+    untouched) equals fill + half-sweep, bit for bit, for both colours."""
+    dom, mb, n = (31, 31, 31), (16, 16, 16), 32
+    g = inputs.rng(52)
+    ba, _ = _ba(gctx, dom, mb)
+    phi, rhs = g.standard_normal((n, n, n)), g.standard_normal((n, n, n))
+    bc = mg.make_bc(periodic)
+    a, b = gu.dense_fab(gctx, ba, phi, 1), gu.dense_fab(gctx, ba, phi, 1)
+    fr = gu.dense_fab(gctx, ba, rhs, 0)
+    for color in (0, 1, 0):
+        mg.mg_fill_boundary(gctx, a, bc)
+        mg.mg_smooth(gctx, a, fr, bc, 1.0 / n, color)
+        mg.mg_smooth(gctx, b, fr, bc, 1.0 / n, color | mg.MG_SMOOTH_DIRECT_READS)
+        assert np.array_equal(gu.fab_dense(gctx, a, phi.shape), gu.fab_dense(gctx, b, phi.shape))
+    uneven, _ = _ba(gctx, (47, 47, 47), (32, 32, 32))
+    c, d = gu.dense_fab(gctx, uneven, np.zeros((48,) * 3), 1), gu.dense_fab(gctx, uneven, np.zeros((48,) * 3), 0)
+    with pytest.raises(mg.MgError):
+        mg.mg_smooth(gctx, c, d, bc, 1.0 / 48, mg.MG_SMOOTH_DIRECT_READS)
+    for f in (a, b, fr, c, d):
+        mg.mg_fab_free(gctx, f)
+
+
+def test_sweep_timing_inside_solves(gctx):
+    n = 64
+    rhs = inputs.dirichlet_jacobi(n, seed=2)
+    ba, _ = _ba(gctx, (n - 1,) * 3, (32, 32, 32))
+    fr, fp = gu.dense_fab(gctx, ba, rhs, 1), mg.mg_fab_alloc(gctx, ba, 1, 2)
+    mg.mg_sweep_timing(gctx, True)
+    res = mg.mg_solve(gctx, fr, fp, mg.make_bc((0, 0, 0)), 1e-10)
+    ms, cnt = mg.mg_sweep_timing(gctx, False)
+    assert res.status == mg.MG_OK and cnt == res.vcycles and ms > 0
+    mg.mg_fab_set_val(gctx, fp, 0.0, True)
+    res2 = mg.mg_solve(gctx, fr, fp, mg.make_bc((0, 0, 0)), 1e-10)
+    assert mg.mg_sweep_timing(gctx, False) == (0.0, 0) and res2.vcycles == res.vcycles
+    mg.mg_fab_free(gctx, fr)
+    mg.mg_fab_free(gctx, fp)
