@@ -291,10 +291,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
 
   // ---------------- consumers ----------------
   // Lane mapping of a plane: lanes per row lpr = smallest power of two >= the row's
-  // x-pairs (at most 32); a warp covers 32 / lpr rows per pass, the 8 warps interleave.
+  // x-pairs (at most 16); a warp covers 32 / lpr rows per pass, the 8 warps interleave.
   const int npv = (S.nx + 1) >> 1;
   int lsh = 0;
-  while ((1 << lsh) < npv && lsh < 5) ++lsh;
+  while ((1 << lsh) < npv && lsh < 4) ++lsh;  // at most 16 lanes per row: pairs of cells
   const int lpr = 1 << lsh;
   const int plane_lane = (tid & 31) & (lpr - 1);
   const int row0 = (tid >> 5) * (32 >> lsh) + ((tid & 31) >> lsh);
@@ -344,26 +344,44 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
         const int oq = (y - S.y0 + 1) * S.pr + S.gr;
         T* p1 = P1 + o;
         T* p0 = P0 + o;
-        for (int x = par + 2 * plane_lane; x < S.nx; x += 2 * lpr) {
-          T zr = p1[x];  // red value above the black cell: new if updated now
+        // cells x and x2 = x + 2 lpr together: both red (or both black), so neither reads
+        // the other; all loads of a pair go before its stores (two independent chains)
+        auto red_sum = [&](int x) {
+          T a = p1[x - 1];
+          a = Ar<T>::add(a, p1[x + 1]);
+          a = Ar<T>::add(a, p1[x - S.pitch]);
+          a = Ar<T>::add(a, p1[x + S.pitch]);
+          a = Ar<T>::add(a, p0[x]);
+          return Ar<T>::add(a, P2[o + x]);
+        };
+        auto black_sum = [&](int x, T zr) {
+          T a = p0[x - 1];
+          a = Ar<T>::add(a, p0[x + 1]);
+          a = Ar<T>::add(a, p0[x - S.pitch]);
+          a = Ar<T>::add(a, p0[x + S.pitch]);
+          a = Ar<T>::add(a, B0[o + x]);
+          return Ar<T>::add(a, zr);
+        };
+        for (int x = par + 2 * plane_lane; x < S.nx; x += 4 * lpr) {
+          const int x2 = x + 2 * lpr;
+          const bool two = x2 < S.nx;
+          const int xb = two ? x2 : x;  // (a harmless repeat of x when there is no second cell)
+          // red values above the black cells: new if updated now
+          T zr1 = p1[x], zr2 = p1[xb];
           if (r_on) {
-            T a = p1[x - 1];
-            a = Ar<T>::add(a, p1[x + 1]);
-            a = Ar<T>::add(a, p1[x - S.pitch]);
-            a = Ar<T>::add(a, p1[x + S.pitch]);
-            a = Ar<T>::add(a, p0[x]);
-            a = Ar<T>::add(a, P2[o + x]);
-            zr = gs_update(a, Q[oq + x], S.mh2);
-            p1[x] = zr;
+            const T a1 = red_sum(x), a2 = red_sum(xb);
+            const T q1 = Q[oq + x], q2 = Q[oq + xb];
+            zr1 = gs_update(a1, q1, S.mh2);
+            zr2 = gs_update(a2, q2, S.mh2);
+            p1[x] = zr1;
+            if (two) p1[x2] = zr2;
           }
           if (b_on) {
-            T a = p0[x - 1];
-            a = Ar<T>::add(a, p0[x + 1]);
-            a = Ar<T>::add(a, p0[x - S.pitch]);
-            a = Ar<T>::add(a, p0[x + S.pitch]);
-            a = Ar<T>::add(a, B0[o + x]);
-            a = Ar<T>::add(a, zr);
-            p0[x] = gs_update(a, QB[oq + x], S.mh2);
+            const T a1 = black_sum(x, zr1), a2 = black_sum(xb, zr2);
+            const T q1 = QB[oq + x], q2 = QB[oq + xb];
+            const T b1 = gs_update(a1, q1, S.mh2), b2 = gs_update(a2, q2, S.mh2);
+            p0[x] = b1;
+            if (two) p0[x2] = b2;
           }
         }
       }
