@@ -88,6 +88,7 @@ struct UnitB {
   long long total = 0;
   size_t off = 0;
   int ty = 1, depth = 3, mp = 0, mpr = 0;
+  bool rhs_smem = true;
   void add(const FusedTable& t) {
     UnitSeg s{};
     s.rows = t.rows.rows();
@@ -100,6 +101,7 @@ struct UnitB {
     depth = std::min(depth, t.depth);
     mp = std::max(mp, t.max_pitch);
     mpr = std::max(mpr, t.max_pitch_r);
+    rhs_smem = rhs_smem && t.rhs_smem;
   }
 };
 struct JobB {
@@ -263,10 +265,10 @@ void smooth_l(Ctx& c, StepLists& S, LevelLists& LL, int sweeps, const unsigned c
     if (LL.fab.total) {
       fill_l(c, S.dt, LL.fill2_phi, dev, s);
       MG_CK(launch_rbgs_fused_l(S.dt, mk(LL.fab, dev), LL.fab.total, LL.fab.ty, LL.fab.depth,
-                                LL.fab.mp, LL.fab.mpr, err, s));
+                                LL.fab.mp, LL.fab.mpr, LL.fab.rhs_smem, err, s));
       fill_l(c, S.dt, LL.fill2_phi2, dev, s);
       MG_CK(launch_rbgs_fused_l(S.dt, mk(LL.fba, dev), LL.fba.total, LL.fba.ty, LL.fba.depth,
-                                LL.fba.mp, LL.fba.mpr, err, s));
+                                LL.fba.mp, LL.fba.mpr, LL.fba.rhs_smem, err, s));
     }
     if (LL.half.total)
       for (int j = 0; j < 2; ++j)

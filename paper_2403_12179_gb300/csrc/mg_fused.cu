@@ -168,13 +168,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-template <class T, int D>
+// RS: rhs staged through shared memory by TMA like phi; else read from global memory (each
+// rhs value is read once per sweep, so staging buys no reuse -- it only costs shared memory).
+template <class T, int D, bool RS>
 __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty_max,
                                                               unsigned phi_buf_elems,
                                                               unsigned rhs_buf_elems,
                                                               int* __restrict__ err) {
   constexpr int NP = 4 + D;  // live phi planes s-2..s+1 plus D in flight
-  constexpr int NR = 2 + D;  // live rhs planes s-1, s plus D in flight
+  constexpr int NR = RS ? 2 + D : 0;  // live rhs planes s-1, s plus D in flight
   extern __shared__ __align__(128) unsigned char smem[];
   T* pbuf = (T*)smem;
   T* rbuf = pbuf + (size_t)NP * phi_buf_elems;
@@ -223,9 +225,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
 
   // planes are loaded in order from z0-2 (phi) / z0-1 (rhs); slot and mbarrier parity
   auto pslot = [&](int p) { return (p - z0 + 2) % NP; };
-  auto rslot = [&](int p) { return (p - z0 + 1) % NR; };
+  auto rslot = [&](int p) { return (p - z0 + 1) % (NR > 0 ? NR : 1); };
   auto pphase = [&](int p) { return (uint32_t)(((p - z0 + 2) / NP) & 1); };
-  auto rphase = [&](int p) { return (uint32_t)(((p - z0 + 1) / NR) & 1); };
+  auto rphase = [&](int p) { return (uint32_t)(((p - z0 + 1) / (NR > 0 ? NR : 1)) & 1); };
   const int s_first = z0 - 1, s_last = z1;  // stages
 
   if (tid >= kConsumers) {
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
       p_issued = p;
     };
     auto issue_rhs = [&](int p) {
-      if (p > rmax) return;
+      if (!RS || p > rmax) return;
       uint64_t* b = &rbar[rslot(p)];
       mbar_expect_tx(b, S.rbytes);
       bulk_load(rbuf + (size_t)rslot(p) * rhs_buf_elems,
@@ -251,7 +253,8 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
     };
     // every slot starts free
     for (int p = z0 - 2; p < z0 - 2 + NP; ++p) issue_phi(p);
-    for (int p = z0 - 1; p < z0 - 1 + NR; ++p) issue_rhs(p);
+    if (RS)
+      for (int p = z0 - 1; p < z0 - 1 + NR; ++p) issue_rhs(p);
     bool ok = true;
     for (int st = s_first; st <= s_last && ok; ++st) {
       const int k = st - s_first;
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
       if (st >= z0) {
         bulk_wait_read1();
         issue_phi(st - 2 + NP);
-        issue_rhs(st - 1 + NR);
+        if (RS) issue_rhs(st - 1 + NR);
       }
     }
     if (!ok) atomicExch(err, 1);  // the consumers time out on their own
@@ -283,8 +286,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
     // slot can still be in flight (earlier phases of a slot cannot be waited on again).
     for (int p = max(z0 - 2, p_issued - NP + 1); p <= p_issued; ++p)
       mbar_wait_bounded(&pbar[pslot(p)], pphase(p));
-    for (int p = max(z0 - 1, r_issued - NR + 1); p <= r_issued; ++p)
-      mbar_wait_bounded(&rbar[rslot(p)], rphase(p));
+    if (RS)
+      for (int p = max(z0 - 1, r_issued - NR + 1); p <= r_issued; ++p)
+        mbar_wait_bounded(&rbar[rslot(p)], rphase(p));
     bulk_wait_all();
     return;
   }
@@ -306,7 +310,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
     bool ok = true;
     for (int p = (s == s_first ? z0 - 2 : s + 1); p <= s + 1; ++p)
       ok = ok && mbar_wait_bounded(&pbar[pslot(p)], pphase(p));
-    ok = ok && mbar_wait_bounded(&rbar[rslot(s)], rphase(s));
+    if (RS) ok = ok && mbar_wait_bounded(&rbar[rslot(s)], rphase(s));
     if (ok) {
     // Stage s red-updates plane s and black-updates plane s-1.  Both passes map (row, x) to
     // the same thread, and the red cell (x, y, s) sits right above the black cell
@@ -316,7 +320,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
     T* P0 = pbuf + (size_t)pslot(s - 1) * phi_buf_elems;
     T* P1 = pbuf + (size_t)pslot(s) * phi_buf_elems;
     const T* P2 = pbuf + (size_t)pslot(s + 1) * phi_buf_elems;
-    const T* Q = rbuf + (size_t)rslot(s) * rhs_buf_elems;
+    // rhs rows as staged: element (x, y) at [(y - y0 + 1) * pr + x + gr]
+    const T* Q = RS ? rbuf + (size_t)rslot(s) * rhs_buf_elems
+                    : rhs + (long long)s * S.planer + (long long)(S.y0 - 1) * S.pr - S.gr;
     // element (x, y) of a phi buffer: [(y - y0 + 2) * pitch + x + g]; rhs: [(y - y0 + 1) * pr + x + gr]
     const int gz = S.loz + s;
     // red rows [ya, yb] of plane s: planes outside [z0, z1) are needed only under the tile
@@ -331,7 +337,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
     }
     const bool black = (s - 1 >= z0 && s - 1 < z1);  // black rows [y0, y0+ty) of plane s-1
     const T* B0 = black ? pbuf + (size_t)pslot(s - 2) * phi_buf_elems : P0;
-    const T* QB = black ? rbuf + (size_t)rslot(s - 1) * rhs_buf_elems : Q;
+    const T* QB = !black ? Q
+                  : RS   ? rbuf + (size_t)rslot(s - 1) * rhs_buf_elems
+                         : rhs + (long long)(s - 1) * S.planer + (long long)(S.y0 - 1) * S.pr - S.gr;
     {
       int y = S.y0 - 1 + row0;
       int par = (S.lox + S.loy + y + gz) & 1;  // first red x >= 0 of row y in plane s
@@ -420,10 +428,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
   }
 }
 
-template <class T, int D>
+template <class T, int D, bool RS>
 static cudaError_t launch_fused_t(const UnitList& L, long long nunits, int ty, int max_pitch,
                                   int max_pitch_r, int* err, cudaStream_t s) {
-  constexpr int NP = 4 + D, NR = 2 + D;
+  constexpr int NP = 4 + D, NR = RS ? 2 + D : 0;
   unsigned pe = (unsigned)((ty + 4) * max_pitch);
   unsigned re = (unsigned)((ty + 2) * max_pitch_r);
   const unsigned align = 128 / sizeof(T);
@@ -433,40 +441,46 @@ static cudaError_t launch_fused_t(const UnitList& L, long long nunits, int ty, i
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   static size_t opted_in = 0;  // largest dynamic shared memory size already allowed
   if (smem > opted_in) {
-    cudaError_t e = cudaFuncSetAttribute(k_rbgs_fused<T, D>,
+    cudaError_t e = cudaFuncSetAttribute(k_rbgs_fused<T, D, RS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     opted_in = smem;
   }
-  k_rbgs_fused<T, D><<<(unsigned)nunits, kFusedThreads, smem, s>>>(L, ty, pe, re, err);
+  k_rbgs_fused<T, D, RS><<<(unsigned)nunits, kFusedThreads, smem, s>>>(L, ty, pe, re, err);
   count_launches(1);
   return cudaGetLastError();
 }
 
-size_t fused_smem_bytes(int dt, int ty, int max_pitch, int max_pitch_r, int depth) {
+size_t fused_smem_bytes(int dt, int ty, int max_pitch, int max_pitch_r, int depth, bool rhs_smem) {
   size_t es = dt == DT_F64 ? 8 : 4;
-  int NP = 4 + depth, NR = 2 + depth;
+  int NP = 4 + depth, NR = rhs_smem ? 2 + depth : 0;
   size_t align = 128 / es;
   size_t pe = ((size_t)(ty + 4) * max_pitch + align - 1) / align * align;
   size_t re = ((size_t)(ty + 2) * max_pitch_r + align - 1) / align * align;
   return (NP * pe + NR * re) * es + (NP + NR + kStageBars) * 8;
 }
 
+template <class T, bool RS>
+static cudaError_t launch_fused_d(const UnitList& L, long long nunits, int ty, int depth,
+                                  int max_pitch, int max_pitch_r, int* err, cudaStream_t s) {
+  if (depth <= 1) return launch_fused_t<T, 1, RS>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+  if (depth == 2) return launch_fused_t<T, 2, RS>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+  return launch_fused_t<T, 3, RS>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+}
+
 cudaError_t launch_rbgs_fused_l(int dt, const UnitList& L, long long nunits, int ty, int depth,
-                                int max_pitch, int max_pitch_r, int* err, cudaStream_t s) {
+                                int max_pitch, int max_pitch_r, bool rhs_smem, int* err,
+                                cudaStream_t s) {
   if (nunits <= 0) return cudaSuccess;
-  if (dt == DT_F64) {
-    if (depth <= 1) return launch_fused_t<double, 1>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
-    if (depth == 2) return launch_fused_t<double, 2>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
-    return launch_fused_t<double, 3>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
-  }
-  if (depth <= 1) return launch_fused_t<float, 1>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
-  if (depth == 2) return launch_fused_t<float, 2>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
-  return launch_fused_t<float, 3>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+  if (dt == DT_F64)
+    return rhs_smem ? launch_fused_d<double, true>(L, nunits, ty, depth, max_pitch, max_pitch_r, err, s)
+                    : launch_fused_d<double, false>(L, nunits, ty, depth, max_pitch, max_pitch_r, err, s);
+  return rhs_smem ? launch_fused_d<float, true>(L, nunits, ty, depth, max_pitch, max_pitch_r, err, s)
+                  : launch_fused_d<float, false>(L, nunits, ty, depth, max_pitch, max_pitch_r, err, s);
 }
 
 cudaError_t launch_rbgs_fused(int dt, const DRow* rows, const int4* units, int nunits, int ty,
-                              int depth, int max_pitch, int max_pitch_r, int* err,
+                              int depth, int max_pitch, int max_pitch_r, bool rhs_smem, int* err,
                               cudaStream_t s) {
   UnitList L{};
   L.one.rows = rows;
@@ -474,7 +488,7 @@ cudaError_t launch_rbgs_fused(int dt, const DRow* rows, const int4* units, int n
   L.one.unit_begin = 0;
   L.one.nunits = nunits;
   L.n = 1;
-  return launch_rbgs_fused_l(dt, L, nunits, ty, depth, max_pitch, max_pitch_r, err, s);
+  return launch_rbgs_fused_l(dt, L, nunits, ty, depth, max_pitch, max_pitch_r, rhs_smem, err, s);
 }
 
 }  // namespace gbmg

@@ -200,10 +200,11 @@ cudaError_t launch_prolong_add(int dt, const DRow* rows, int nbox, long long nro
 // filled), v[1] = rhs (1 ghost layer, filled), v[2] = destination phi with the source's
 // layout; pad_ = Dirichlet-face flags (bit d: low face of dim d, bit 3+d: high face).
 // units[i] = {box, y0, z0, z1}: rows [y0, y0+ty) x planes [z0, z1) of a box; depth = planes
-// loaded ahead (1 to 3).
-size_t fused_smem_bytes(int dt, int ty, int max_pitch, int max_pitch_r, int depth);
+// loaded ahead (1 to 3).  rhs_smem: rhs staged through shared memory too (else read from
+// global memory).
+size_t fused_smem_bytes(int dt, int ty, int max_pitch, int max_pitch_r, int depth, bool rhs_smem);
 cudaError_t launch_rbgs_fused(int dt, const DRow* rows, const int4* units, int nunits, int ty,
-                              int depth, int max_pitch, int max_pitch_r, int* err,
+                              int depth, int max_pitch, int max_pitch_r, bool rhs_smem, int* err,
                               cudaStream_t s);
 
 cudaError_t launch_bottom(int dt, const BottomJob* jobs, int njobs, int maxN, cudaStream_t s);
@@ -260,6 +261,7 @@ cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,
 cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsigned long long* norms,
                                  cudaStream_t s);
 cudaError_t launch_rbgs_fused_l(int dt, const UnitList& L, long long nunits, int ty, int depth,
-                                int max_pitch, int max_pitch_r, int* err, cudaStream_t s);
+                                int max_pitch, int max_pitch_r, bool rhs_smem, int* err,
+                                cudaStream_t s);
 
 }  // namespace gbmg

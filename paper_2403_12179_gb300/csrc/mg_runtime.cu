@@ -121,10 +121,13 @@ void Ctx::load_tune_file() {
   if (!path || !*path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  char key[200];
-  FusedCfg cfg;
-  while (std::fscanf(f, "%199s %d %d %d", key, &cfg.ty, &cfg.zc, &cfg.depth) == 4)
-    if (cfg.ty > 0 && cfg.zc > 0 && cfg.depth >= 1 && cfg.depth <= 3) tune[key] = cfg;
+  char line[400], key[200];
+  while (std::fgets(line, sizeof line, f)) {
+    FusedCfg cfg;
+    if (std::sscanf(line, "%199s %d %d %d %d", key, &cfg.ty, &cfg.zc, &cfg.depth, &cfg.rhs_smem) == 5 &&
+        cfg.ty > 0 && cfg.zc > 0 && cfg.depth >= 1 && cfg.depth <= 3)
+      tune[key] = cfg;
+  }
   std::fclose(f);
 }
 
@@ -133,7 +136,7 @@ void Ctx::save_tune_entry(const std::string& key, const FusedCfg& cfg) {
   if (!path || !*path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d\n", key.c_str(), cfg.ty, cfg.zc, cfg.depth);
+  std::fprintf(f, "%s %d %d %d %d\n", key.c_str(), cfg.ty, cfg.zc, cfg.depth, cfg.rhs_smem);
   std::fclose(f);
 }
 
@@ -390,7 +393,9 @@ static FusedTable build_fused(Ctx& c, const BoxArray& ba, double h, const FabObj
   t.ty = std::max(1, std::min(cfg.ty, maxn1));
   t.zc = std::max(1, std::min(cfg.zc, maxn2));
   t.depth = cfg.depth;
-  if (fused_smem_bytes(src.dtype, t.ty, t.max_pitch, t.max_pitch_r, t.depth) > 200 * 1024) return t;
+  t.rhs_smem = cfg.rhs_smem != 0;
+  if (fused_smem_bytes(src.dtype, t.ty, t.max_pitch, t.max_pitch_r, t.depth, t.rhs_smem) > 200 * 1024)
+    return t;
   std::vector<DRow> rows;
   long long nr = 0;
   append_rows(&rows, &nr, ba, 0, h, 0, [&](int b, DRow& R) {
@@ -433,7 +438,7 @@ FusedTable make_fused(Ctx& c, const BoxArray& ba, double h, const FabObj& src, c
     mpr = std::max(mpr, rhs.lay.pitch[b]);
   }
   char key[160];
-  std::snprintf(key, sizeof key, "dt%d_b%dx%dx%d_n%zu_p%d_%d_g%d_%d", src.dtype, mx[0], mx[1], mx[2],
+  std::snprintf(key, sizeof key, "v2_dt%d_b%dx%dx%d_n%zu_p%d_%d_g%d_%d", src.dtype, mx[0], mx[1], mx[2],
                 ba.boxes.size(), mp, mpr, src.lay.g, rhs.lay.g);
   {
     std::lock_guard<std::mutex> lk(c.tune_mu);
@@ -447,12 +452,13 @@ FusedTable make_fused(Ctx& c, const BoxArray& ba, double h, const FabObj& src, c
   cudaEvent_t e0, e1;
   MG_CK(cudaEventCreate(&e0));
   MG_CK(cudaEventCreate(&e1));
+  for (int rs : {1, 0})
   for (int depth : {2, 3})
     for (int ty : {4, 8, 16, 32}) {
       if (ty > 2 * mx[1] && ty != 4) continue;
       for (int zc : {8, 16, 32, 64}) {
         if (zc > 2 * mx[2] && zc != 8) continue;
-        FusedTable t = build_fused(c, ba, h, src, rhs, dst, periodic, FusedCfg{ty, zc, depth}, s);
+        FusedTable t = build_fused(c, ba, h, src, rhs, dst, periodic, FusedCfg{ty, zc, depth, rs}, s);
         if (!t.ok) continue;
         launch_fused(c, t, src.dtype, s);  // warm
         MG_CK(cudaEventRecord(e0, s));
@@ -463,7 +469,7 @@ FusedTable make_fused(Ctx& c, const BoxArray& ba, double h, const FabObj& src, c
         MG_CK(cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best_ms) {
           best_ms = ms;
-          best = FusedCfg{t.ty, t.zc, t.depth};
+          best = FusedCfg{t.ty, t.zc, t.depth, t.rhs_smem ? 1 : 0};
           best_t = std::move(t);
         }
       }
@@ -482,7 +488,7 @@ FusedTable make_fused(Ctx& c, const BoxArray& ba, double h, const FabObj& src, c
 
 void launch_fused(Ctx& c, const FusedTable& t, int dt, cudaStream_t s) {
   MG_CK(launch_rbgs_fused(dt, t.rows.rows(), (const int4*)t.units->p, t.nunits, t.ty, t.depth,
-                          t.max_pitch, t.max_pitch_r, (int*)c.d_err->p, s));
+                          t.max_pitch, t.max_pitch_r, t.rhs_smem, (int*)c.d_err->p, s));
 }
 
 const FusedTable& fused_table(Ctx& c, int64_t src_id, FabObj& src, int64_t rhs_id, FabObj& rhs,

@@ -137,9 +137,10 @@ struct OpTable {
 
 struct Hierarchy;
 
-// Launch configuration of the fused sweep: tile rows, z-planes per CTA, prefetch depth.
+// Launch configuration of the fused sweep: tile rows, z-planes per CTA, prefetch depth, rhs
+// staged through shared memory (1) or read from global memory (0).
 struct FusedCfg {
-  int ty = 16, zc = 16, depth = 2;
+  int ty = 16, zc = 16, depth = 2, rhs_smem = 1;
 };
 
 struct Ctx {
@@ -268,6 +269,7 @@ struct FusedTable {
   OpTable rows;
   DevBufP units;
   int nunits = 0, ty = 16, zc = 16, depth = 2, max_pitch = 0, max_pitch_r = 0;
+  bool rhs_smem = true;
   std::vector<int64_t> owner_fabs;  // for cache invalidation
 };
 bool fused_eligible(const FabObj& phi, const FabObj& rhs);

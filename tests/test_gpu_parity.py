@@ -579,3 +579,42 @@ def test_sweep_timing_inside_solves(gctx):
     assert mg.mg_sweep_timing(gctx, False) == (0.0, 0) and res2.vcycles == res.vcycles
     mg.mg_fab_free(gctx, fr)
     mg.mg_fab_free(gctx, fp)
+
+
+@pytest.mark.parametrize("rhs_smem", [1, 0])
+@pytest.mark.parametrize("dt", [mg.MG_F64, mg.MG_F32])
+def test_fused_sweep_rhs_staging_forced(orc, tmp_path, monkeypatch, rhs_smem, dt):
+    """Both ways the fused sweep reads rhs (staged through shared memory by TMA, or from global
+    memory), forced through the tuning file, equal the oracle's fill-red-fill-black."""
+    import paper_2403_12179_gb300.build as b
+    b.build()
+    dom, mb = (31, 23, 15), (16, 12, 16)
+    es = 8 if dt == mg.MG_F64 else 4
+    align = 16 // es
+    pitch = lambda n, g: (n + 2 * g + align - 1) // align * align
+    key = f"v2_dt{dt}_b16x12x16_n4_p{pitch(16, 2)}_{pitch(16, 1)}_g2_1"
+    tune = tmp_path / "tune.txt"
+    tune.write_text(f"{key} 4 8 2 {rhs_smem}\n")
+    monkeypatch.setenv("GBMG_TUNE_FILE", str(tune))
+    ctx = mg.mg_init(0)
+    try:
+        npdt = np.float64 if dt == mg.MG_F64 else np.float32
+        ba, boxes = _ba(ctx, dom, mb)
+        assert len(boxes) == 4
+        g = inputs.rng(53)
+        phi = [g.standard_normal(f.shape).astype(npdt) for f in orc.new_field(boxes, 2)]
+        rhs = [g.standard_normal(f.shape).astype(npdt) for f in orc.new_field(boxes, 1)]
+        ref = phi
+        for color in (0, 1):
+            ref = orc.fill_boundary(Z3, dom, (0, 1, 0), boxes, ref, 2)
+            ref = orc.rbgs(Z3, dom, boxes, 1.0 / 32, ref, 2, rhs, 1, color)
+        bc = mg.make_bc((0, 1, 0))
+        fa, fr = gu.to_fab(ctx, ba, phi, 2, dt), gu.to_fab(ctx, ba, rhs, 1, dt)
+        fb = mg.mg_fab_alloc(ctx, ba, 1, 2, dt)
+        mg.mg_fill_boundary(ctx, fa, bc)
+        mg.mg_fill_boundary(ctx, fr, bc)
+        mg.mg_smooth_fused(ctx, fa, fr, fb, bc, 1.0 / 32)
+        for a, r in zip(gu.from_fab(ctx, fb, len(boxes)), ref):
+            assert np.array_equal(gu.valid(a, 2), gu.valid(r, 2))
+    finally:
+        mg.mg_finalize(ctx)
