@@ -55,12 +55,15 @@ struct SegB {
   long long total = 0;
   size_t off = 0;
   bool direct = false;  // some member's rows carry box-face reads
+  int width = 0;
   void add(const OpTable& t, int slot) {
     if (!t.nrows) return;
     direct = direct || t.direct;
+    width = std::max(width, t.width);
     Seg s{};
     s.rows = t.rows();
     s.row_begin = total;
+    s.row_count = t.nrows;
     s.nbox = t.nbox;
     s.slot = slot;
     v.push_back(s);
@@ -158,6 +161,7 @@ struct Staging {
 SegList mk(const SegB& b, const unsigned char* dev) {
   SegList L{};
   L.n = (int)b.v.size();
+  L.width = b.width;
   if (L.n == 1) L.one = b.v[0];
   else L.segs = (const Seg*)(dev + b.off);
   return L;

@@ -76,6 +76,11 @@ bool validate(const BoxArray& ba, std::string* err) {
   if (ba.boxes.empty()) { *err = "no boxes"; return false; }
   for (const Box& b : ba.boxes) {
     if (b.empty()) { *err = "empty box " + fmt_box(b); return false; }
+    // the device kernels index a box's x-rows (ghosts included) with 32-bit integers
+    if ((int64_t)(b.len(1) + 8) * (b.len(2) + 8) >= ((int64_t)1 << 30)) {
+      *err = "box " + fmt_box(b) + " has too many x-rows";
+      return false;
+    }
     Box i = intersect(b, ba.dom);
     if (i.npts() != b.npts() || i.empty()) {
       *err = "box " + fmt_box(b) + " leaves the domain " + fmt_box(ba.dom);

@@ -70,7 +70,17 @@ __device__ __forceinline__ T residual_of(T s, T phi, T rhs, T ih2) {
 constexpr int kWarps = 8;  // warps per block in the row kernels
 constexpr int kThreads = kWarps * 32;
 
-__device__ __forceinline__ int find_box(const DRow* __restrict__ rows, int nbox, long long r) {
+// Box of segment row r (0 <= r < cnt).  Boxes of equal row counts (the usual case) are found
+// by the proportional guess, checked with two independent loads; else binary search.
+__device__ __forceinline__ int find_box(const DRow* __restrict__ rows, int nbox, long long r,
+                                        long long cnt) {
+  if (cnt > 0 && cnt * nbox < (1ll << 32)) {
+    int g = (int)((unsigned)(r * nbox) / (unsigned)cnt);
+    g = g < nbox - 1 ? g : nbox - 1;
+    const long long a = rows[g].row0;
+    const long long e = g + 1 < nbox ? rows[g + 1].row0 : cnt;
+    if (a <= r && r < e) return g;
+  }
   int lo = 0, hi = nbox - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
@@ -88,15 +98,15 @@ __device__ __forceinline__ int find_seg(const Seg* __restrict__ segs, int n, lon
   return lo;
 }
 
-// Block k owns launch rows [k*per, (k+1)*per); with HW = 1 warp w of the block takes rows
-// begin+w, +kWarps, ...; with HW = 2 each half-warp takes its own row (begin + 2w + half,
-// step 2 kWarps).  f(row, row-within-box, slot) is called once per row with all lanes of the
-// (half-)warp active.
+// Block k owns launch rows [k*per, (k+1)*per).  A warp is split into HW lane groups of
+// 32 / HW lanes, each with its own row: group q of warp w takes rows begin + HW*w + q, step
+// HW*kWarps.  f(row, row-within-box, slot) is called once per row with all lanes of the
+// group active.
 template <int HW = 1, class F>
 __device__ __forceinline__ void for_rows(const SegList& L, long long nrows, long long per, F&& f) {
   long long begin = (long long)blockIdx.x * per;
   long long end = begin + per < nrows ? begin + per : nrows;
-  long long r = begin + (long long)(threadIdx.x >> 5) * HW + (HW == 2 ? ((threadIdx.x >> 4) & 1) : 0);
+  long long r = begin + (long long)(threadIdx.x >> 5) * HW + (int)((threadIdx.x & 31) / (32 / HW));
   if (r >= end) return;
   int si = 0;
   Seg S = L.one;
@@ -104,7 +114,7 @@ __device__ __forceinline__ void for_rows(const SegList& L, long long nrows, long
     si = find_seg(L.segs, L.n, r);
     S = L.segs[si];
   }
-  int b = find_box(S.rows, S.nbox, r - S.row_begin);
+  int b = find_box(S.rows, S.nbox, r - S.row_begin, L.n > 1 ? S.row_count : nrows);
   for (; r < end; r += kWarps * HW) {
     if (L.n > 1) {
       bool moved = false;
@@ -299,7 +309,9 @@ __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
 }
 
 // Red-black Gauss-Seidel half-sweep: cells with (i+j+k) mod 2 == color (global indices)
-// take phi = (s - h^2 rhs) / 6.  Lane l of a warp updates cells par + 2l (+64 k) of a line.
+// take phi = (s - h^2 rhs) / 6.  G lanes per x-line (16 for wide boxes, fewer for narrow
+// ones so that every lane has two cells): lane l updates cells par + 2l + 4Gk and
+// par + 2l + 4Gk + 2G together.
 // DIRECT: box-face neighbours through DRow::nbd / nbf (rows without that information read
 // their ghost cells); else ghost cells, through plain offsets.
 // norms != null (single-segment launches, DIRECT only): also the max-norm of the residual of
@@ -308,18 +320,18 @@ __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
 // except where a read is the cell's own value negated (a Dirichlet face): those cells sum
 // again, reading their new value.  (With an odd periodic extent an image could be the cell's
 // own colour; callers use this on even periodic extents only.)
-template <class T, bool DIRECT, bool NORM = false>
+template <class T, bool DIRECT, bool NORM, int G>
 __global__ void __launch_bounds__(kThreads, 4) k_rbgs_half(SegList L, long long nrows, long long per,
                                                         int color, unsigned long long* norms) {
-  // Half a warp per row; a lane updates cells x and x + 32 of a pair step together (both red:
-  // their neighbours are black and unchanged, so both loads go first -- two independent FP64
-  // chains per lane).
-  const int sub = threadIdx.x & 15;
+  // A lane updates cells x and x + 2G of a pair step together (both of this colour: their
+  // neighbours are of the other colour and unchanged, so both loads go first -- two
+  // independent FP64 chains per lane).
+  const int sub = threadIdx.x & (G - 1);
   unsigned long long mx = 0;
   int cur = -1;
-  for_rows<2>(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
+  for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
     const int n0 = R.n[0], n1 = R.n[1];
-    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const int y = (int)lr % n1, z = (int)lr / n1;
     T* phi = line<T>(R.v[0], y, z);
     const T* rhs = line<T>(R.v[1], y, z);
     const T h2 = (T)R.h2, ih2 = (T)R.ih2;
@@ -330,8 +342,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_rbgs_half(SegList L, long long 
       mx = k > mx ? k : mx;
     };
     auto sweep = [&](auto&& sum, auto&& resum) {
-      for (int x = par + 2 * sub; x < n0; x += 64) {
-        const int x2 = x + 32;
+      for (int x = par + 2 * sub; x < n0; x += 4 * G) {
+        const int x2 = x + 2 * G;
         const bool two = x2 < n0;
         const T s1 = sum(x);
         const T s2 = two ? sum(x2) : T(0);
@@ -384,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, DIRECT ? 4 : 6) k_residual(SegList L
       mx = 0;
     }
     const int n0 = R.n[0], n1 = R.n[1];
-    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const int y = (int)lr % n1, z = (int)lr / n1;
     const T* phi = line<T>(R.v[0], y, z);
     const T* rhs = line<T>(R.v[1], y, z);
     T* r = R.v[2].p ? line<T>(R.v[2], y, z) : nullptr;
@@ -412,21 +424,22 @@ __global__ void __launch_bounds__(kThreads, DIRECT ? 4 : 6) k_residual(SegList L
   if (norms) flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
 }
 
-// Fused residual + restriction.  Lane l of a warp produces coarse cells X = l, l+32, ... of
-// one coarse x-line: the 8 child residuals summed x fastest, times 1/8.
-template <class T, bool DIRECT>
+// Fused residual + restriction.  G lanes per coarse x-line (32, or fewer for narrow boxes):
+// lane l produces coarse cells X = l, l+G, ...: the 8 child residuals summed x fastest,
+// times 1/8.
+template <class T, bool DIRECT, int G>
 __global__ void __launch_bounds__(kThreads) k_residual_restrict(SegList L, long long nrows,
                                                                 long long per) {
-  const int lane = threadIdx.x & 31;
-  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
+  const int lane = threadIdx.x & (G - 1);
+  for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int nc0 = R.n[0] >> 1, nc1 = R.n[1] >> 1;
-    const int Y = (int)(lr % nc1), Z = (int)(lr / nc1);
+    const int Y = (int)lr % nc1, Z = (int)lr / nc1;
     const DView vp = R.v[0], vr = R.v[1];
     const T ih2 = (T)R.ih2;
     T* crhs = line<T>(R.c[0], Y, Z);
     T* cphi = R.c[1].p ? line<T>(R.c[1], Y, Z) : nullptr;
     const int n0 = R.n[0];
-    for (int X = lane; X < nc0; X += 32) {
+    for (int X = lane; X < nc0; X += G) {
       T acc = T(0);
 #pragma unroll
       for (int k = 0; k < 2; ++k)
@@ -455,7 +468,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(SegList L, long long nrow
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int nc0 = R.n[0] >> 1, nc1 = R.n[1] >> 1;
-    const int Y = (int)(lr % nc1), Z = (int)(lr / nc1);
+    const int Y = (int)lr % nc1, Z = (int)lr / nc1;
     T* c = line<T>(R.c[0], Y, Z);
     for (int X = lane; X < nc0; X += 32) {
       T acc = T(0);
@@ -473,17 +486,18 @@ __global__ void __launch_bounds__(kThreads) k_restrict(SegList L, long long nrow
   });
 }
 
-// fine(c) += coarse(floor(c / 2)); c[0] addresses coarse cell floor(lo / 2).
-template <class T>
+// fine(c) += coarse(floor(c / 2)); c[0] addresses coarse cell floor(lo / 2).  G lanes per
+// fine x-line.
+template <class T, int G>
 __global__ void __launch_bounds__(kThreads) k_prolong_add(SegList L, long long nrows, long long per) {
-  const int lane = threadIdx.x & 31;
-  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
+  const int lane = threadIdx.x & (G - 1);
+  for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
-    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const int y = (int)lr % n1, z = (int)lr / n1;
     const int ox = R.lo[0] & 1, oy = R.lo[1] & 1, oz = R.lo[2] & 1;
     T* f = line<T>(R.v[0], y, z);
     const T* c = line<T>(R.c[0], (y + oy) >> 1, (z + oz) >> 1);
-    for (int x = lane; x < n0; x += 32) f[x] = Ar<T>::add(f[x], c[(x + ox) >> 1]);
+    for (int x = lane; x < n0; x += G) f[x] = Ar<T>::add(f[x], c[(x + ox) >> 1]);
   });
 }
 
@@ -493,7 +507,7 @@ __global__ void __launch_bounds__(kThreads) k_set_valid(SegList L, long long nro
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
-    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const int y = (int)lr % n1, z = (int)lr / n1;
     T* f = line<T>(R.v[0], y, z);
     for (int x = lane; x < n0; x += 32) f[x] = value;
   });
@@ -530,7 +544,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_copy(SegList L, long long nr
   const long long dplane = (long long)dn.x * dn.y, dcomp = dplane * dn.z;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
-    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const int y = (int)lr % n1, z = (int)lr / n1;
     T* f = line<T>(R.v[0], y, z);
     T* d = dense + (long long)(R.lo[2] + z - dlo.z) * dplane +
            (long long)(R.lo[1] + y - dlo.y) * dn.x + (R.lo[0] - dlo.x);
@@ -563,7 +577,7 @@ __global__ void __launch_bounds__(kThreads) k_maxabs(SegList L, long long nrows,
       mx = 0;
     }
     const int n0 = R.n[0], n1 = R.n[1];
-    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const int y = (int)lr % n1, z = (int)lr / n1;
     const T* f = line<T>(R.v[0], y, z);
     for (int x = lane; x < n0; x += 32) {
       unsigned long long k = Ar<T>::abskey(f[x]);
@@ -589,7 +603,7 @@ __global__ void __launch_bounds__(kThreads) k_scale_residual_f32(SegList L, long
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
     const int n0 = R.n[0], n1 = R.n[1];
-    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const int y = (int)lr % n1, z = (int)lr / n1;
     const double* __restrict__ r = line<double>(R.v[0], y, z);
     float* __restrict__ r32 = line<float>(R.c[0], y, z);
     float* __restrict__ e32 = line<float>(R.c[1], y, z);
@@ -607,7 +621,7 @@ __global__ void __launch_bounds__(kThreads) k_correct_add(SegList L, long long n
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
     const int n0 = R.n[0], n1 = R.n[1];
-    const int y = (int)(lr % n1), z = (int)(lr / n1);
+    const int y = (int)lr % n1, z = (int)lr / n1;
     double* __restrict__ phi = line<double>(R.v[0], y, z);
     const float* __restrict__ e = line<float>(R.c[0], y, z);
     const double up = pow2_floor(norm_of(norms, slot + R.solve));
@@ -632,10 +646,12 @@ struct Grid {
   unsigned blocks;
 };
 
-Grid row_grid(long long nrows, int blocks_per_sm) {
+// rows_per_pass: rows a block takes at once (kWarps x lane groups per warp); per is a
+// multiple of it so that only a launch's last block has idle groups.
+Grid row_grid(long long nrows, int blocks_per_sm, int rows_per_pass = kWarps) {
   long long target = (long long)num_sms() * blocks_per_sm;
   long long per = (nrows + target - 1) / target;
-  if (per < kWarps) per = kWarps;
+  per = (per + rows_per_pass - 1) / rows_per_pass * rows_per_pass;
   Grid g;
   g.per = per;
   g.blocks = (unsigned)((nrows + per - 1) / per);
@@ -701,16 +717,52 @@ cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int n
   return launch_copy_tags_l(dt, L, nchunks, ncomp, s);
 }
 
+namespace {
+// Blocks per SM the stencil row kernels aim for (measured: 16 beats 8 and 4 on both the
+// finest and the coarser levels).
+constexpr int kRowBlocksPerSM = 16;
+
+// Lanes per x-line for a launch whose widest line holds `width` cells (0 = unknown): the
+// smallest group (of those the kernels are built for) whose lanes each get `cells`
+// consecutive-pass cells at most, i.e. width / cells lanes rounded up.
+int group_lanes(int width, int cells, int lo, int hi) {
+  if (width <= 0) return hi;
+  int g = lo;
+  while (g < hi && g * cells < width) g *= 2;
+  return g;
+}
+
+template <class T, bool DIRECT>
+void rbgs_half_g(int G, const Grid& g, cudaStream_t s, const SegList& L, long long nrows, int color,
+                 unsigned long long* norms) {
+  if (G == 16) k_rbgs_half<T, DIRECT, false, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+  else if (G == 8) k_rbgs_half<T, DIRECT, false, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+  else k_rbgs_half<T, DIRECT, false, 4><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+}
+template <class T>
+void rbgs_half_norm_g(int G, const Grid& g, cudaStream_t s, const SegList& L, long long nrows, int color,
+                      unsigned long long* norms) {
+  if (G == 16) k_rbgs_half<T, true, true, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+  else k_rbgs_half<T, true, true, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+}
+}  // namespace
+
 cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int color, cudaStream_t s,
                                bool direct, unsigned long long* norms) {
   if (nrows <= 0) return cudaSuccess;
   if (norms && (L.n != 1 || !direct)) return cudaErrorInvalidValue;
-  Grid g = row_grid(nrows, 16);
+  // a line of w cells holds w / 2 of one colour; two per lane
+  const int G = group_lanes(L.width, 4, norms ? 8 : 4, 16);
+  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
   if (norms) {
-    if (dt == DT_F64) k_rbgs_half<double, true, true><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
-    else k_rbgs_half<float, true, true><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+    if (dt == DT_F64) rbgs_half_norm_g<double>(G, g, s, L, nrows, color, norms);
+    else rbgs_half_norm_g<float>(G, g, s, L, nrows, color, norms);
+  } else if (dt == DT_F64) {
+    if (direct) rbgs_half_g<double, true>(G, g, s, L, nrows, color, norms);
+    else rbgs_half_g<double, false>(G, g, s, L, nrows, color, norms);
   } else {
-    GB_DISPATCH_D(dt, direct, k_rbgs_half, g.blocks, kThreads, 0, s, L, nrows, g.per, color, norms);
+    if (direct) rbgs_half_g<float, true>(G, g, s, L, nrows, color, norms);
+    else rbgs_half_g<float, false>(G, g, s, L, nrows, color, norms);
   }
   count_launches(1);
   return cudaGetLastError();
@@ -725,18 +777,43 @@ cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigne
   return cudaGetLastError();
 }
 
+namespace {
+template <class T, bool DIRECT>
+void residual_restrict_g(int G, const Grid& g, cudaStream_t s, const SegList& L, long long nrows) {
+  if (G == 32) k_residual_restrict<T, DIRECT, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+  else if (G == 16) k_residual_restrict<T, DIRECT, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+  else k_residual_restrict<T, DIRECT, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+}
+template <class T>
+void prolong_add_g(int G, const Grid& g, cudaStream_t s, const SegList& L, long long nrows) {
+  if (G == 32) k_prolong_add<T, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+  else if (G == 16) k_prolong_add<T, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+  else k_prolong_add<T, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+}
+}  // namespace
+
 cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s, bool direct) {
   if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 16);
-  GB_DISPATCH_D(dt, direct, k_residual_restrict, g.blocks, kThreads, 0, s, L, nrows, g.per);
+  // rows are coarse lines of width / 2 cells, one per lane
+  const int G = group_lanes(L.width, 2, 8, 32);
+  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  if (dt == DT_F64) {
+    if (direct) residual_restrict_g<double, true>(G, g, s, L, nrows);
+    else residual_restrict_g<double, false>(G, g, s, L, nrows);
+  } else {
+    if (direct) residual_restrict_g<float, true>(G, g, s, L, nrows);
+    else residual_restrict_g<float, false>(G, g, s, L, nrows);
+  }
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 16);
-  GB_DISPATCH(dt, k_prolong_add, g.blocks, kThreads, 0, s, L, nrows, g.per);
+  const int G = group_lanes(L.width, 1, 8, 32);
+  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  if (dt == DT_F64) prolong_add_g<double>(G, g, s, L, nrows);
+  else prolong_add_g<float>(G, g, s, L, nrows);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -780,8 +857,8 @@ cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsign
 // ---- single-table launchers (one segment) ------------------------------------------------
 
 cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
-                             cudaStream_t s, bool direct, unsigned long long* norms) {
-  return launch_rbgs_half_l(dt, one_seg(rows, nbox), nrows, color, s, direct, norms);
+                             cudaStream_t s, bool direct, unsigned long long* norms, int width) {
+  return launch_rbgs_half_l(dt, one_seg(rows, nbox, 0, width), nrows, color, s, direct, norms);
 }
 
 cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
@@ -790,8 +867,8 @@ cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
 }
 
 cudaError_t launch_residual_restrict(int dt, const DRow* rows, int nbox, long long nrows,
-                                     cudaStream_t s, bool direct) {
-  return launch_residual_restrict_l(dt, one_seg(rows, nbox), nrows, s, direct);
+                                     cudaStream_t s, bool direct, int width) {
+  return launch_residual_restrict_l(dt, one_seg(rows, nbox, 0, width), nrows, s, direct);
 }
 
 cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows, cudaStream_t s) {
@@ -803,8 +880,8 @@ cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows,
 }
 
 cudaError_t launch_prolong_add(int dt, const DRow* rows, int nbox, long long nrows,
-                               cudaStream_t s) {
-  return launch_prolong_add_l(dt, one_seg(rows, nbox), nrows, s);
+                               cudaStream_t s, int width) {
+  return launch_prolong_add_l(dt, one_seg(rows, nbox, 0, width), nrows, s);
 }
 
 cudaError_t launch_bottom(int dt, const BottomJob* jobs, int njobs, int maxN, cudaStream_t s) {

@@ -110,6 +110,7 @@ __host__ __device__ inline int tag_chunk_rows(int ex, int ncomp) {
 struct Seg {
   const DRow* rows;
   long long row_begin;  // first launch row of this segment
+  long long row_count;  // rows of this segment (0: the launch's row count)
   int nbox;
   int slot;
 };
@@ -117,14 +118,17 @@ struct SegList {
   const Seg* segs;  // device array, used when n > 1
   Seg one;          // the segment when n == 1
   int n;
+  int width;        // host hint: widest box x-extent (cells) in the launch, 0 = unknown; the
+                    // launchers size the lane groups of narrow rows from it
 };
-inline SegList one_seg(const DRow* rows, int nbox, int slot = 0) {
+inline SegList one_seg(const DRow* rows, int nbox, int slot = 0, int width = 0) {
   SegList L{};
   L.one.rows = rows;
   L.one.row_begin = 0;
   L.one.nbox = nbox;
   L.one.slot = slot;
   L.n = 1;
+  L.width = width;
   return L;
 }
 
@@ -172,10 +176,11 @@ cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int n
 // the ghost cells (filled beforehand) through plain offsets.
 // v[0] = phi, v[1] = rhs.  norms != null (direct, single-table launches only): also atomicMax
 // of |residual| of every updated cell after its update into norms[solve] (valid when the
-// box array's periodic extents are even).
+// box array's periodic extents are even).  width: the widest box x-extent of the table
+// (0 = unknown; any value gives the same results, it only picks the lanes per row).
 cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
                              cudaStream_t s, bool direct = false,
-                             unsigned long long* norms = nullptr);
+                             unsigned long long* norms = nullptr, int width = 0);
 
 // v[0] = phi, v[1] = rhs, v[2] = r (p == null: not stored).  norms[solve] receives
 // atomicMax of the bit pattern of |r| (NaN propagates as the largest pattern).  color < 0:
@@ -187,14 +192,14 @@ cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
 // Rows are coarse x-lines.  v[0] = phi, v[1] = rhs (fine); c[0] = coarse rhs,
 // c[1] = coarse phi (p == null: not zeroed).
 cudaError_t launch_residual_restrict(int dt, const DRow* rows, int nbox, long long nrows,
-                                     cudaStream_t s, bool direct = false);
+                                     cudaStream_t s, bool direct = false, int width = 0);
 
 // Rows are coarse x-lines.  v[0] = fine field; c[0] = coarse field.
 cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows, cudaStream_t s);
 
 // Rows are fine x-lines.  v[0] = fine field (+=); c[0] = coarse field.
 cudaError_t launch_prolong_add(int dt, const DRow* rows, int nbox, long long nrows,
-                               cudaStream_t s);
+                               cudaStream_t s, int width = 0);
 
 // Fused red + black sweep (see mg_fused.cu).  Rows: v[0] = source phi (2 ghost layers,
 // filled), v[1] = rhs (1 ghost layer, filled), v[2] = destination phi with the source's

@@ -317,6 +317,7 @@ OpTable upload_table(Ctx& c, const std::vector<DRow>& rows, long long nrows, cud
   OpTable t;
   t.nbox = (int)rows.size();
   t.nrows = nrows;
+  for (const DRow& R : rows) t.width = std::max(t.width, R.n[0]);
   if (!rows.empty()) t.d = c.upload(rows.data(), rows.size() * sizeof(DRow), s);
   return t;
 }
@@ -1077,7 +1078,7 @@ int mg_smooth(mg_ctx_t h, mg_fab_t phi, mg_fab_t rhs, const mg_bc* bc, double hh
           tt.direct = true;
           return tt;
         });
-        MG_CK(launch_rbgs_half(fp->dtype, t.rows(), t.nbox, t.nrows, color & 1, s, true));
+        MG_CK(launch_rbgs_half(fp->dtype, t.rows(), t.nbox, t.nrows, color & 1, s, true, nullptr, t.width));
         return MG_OK;
       }
     }
@@ -1106,11 +1107,11 @@ int mg_smooth(mg_ctx_t h, mg_fab_t phi, mg_fab_t rhs, const mg_bc* bc, double hh
       }
     }
     if (color < 2) {
-      MG_CK(launch_rbgs_half(fp->dtype, t.rows(), t.nbox, t.nrows, color, s));
+      MG_CK(launch_rbgs_half(fp->dtype, t.rows(), t.nbox, t.nrows, color, s, false, nullptr, t.width));
     } else {
       for (int col = 0; col < 2; ++col) {
         launch_fill(*c, *fp, bc, s);
-        MG_CK(launch_rbgs_half(fp->dtype, t.rows(), t.nbox, t.nrows, col, s));
+        MG_CK(launch_rbgs_half(fp->dtype, t.rows(), t.nbox, t.nrows, col, s, false, nullptr, t.width));
       }
     }
     return MG_OK;
@@ -1203,7 +1204,7 @@ int mg_residual_restrict(mg_ctx_t h, mg_fab_t phi, mg_fab_t rhs, mg_fab_t crhs, 
         if (fz) R.c[1] = coarse_view(*fz, map[b], F.boxes[b]);
       }, c->stream);
     });
-    MG_CK(launch_residual_restrict(fp->dtype, t.rows(), t.nbox, t.nrows, s));
+    MG_CK(launch_residual_restrict(fp->dtype, t.rows(), t.nbox, t.nrows, s, false, t.width));
     return MG_OK;
   });
 }
@@ -1246,7 +1247,7 @@ int mg_prolong_add(mg_ctx_t h, mg_fab_t coarse, mg_fab_t fine, void* stream) {
         R.c[0] = coarse_view(*fc, map[b], F.boxes[b]);
       }, c->stream);
     });
-    MG_CK(launch_prolong_add(ff->dtype, t.rows(), t.nbox, t.nrows, s));
+    MG_CK(launch_prolong_add(ff->dtype, t.rows(), t.nbox, t.nrows, s, t.width));
     return MG_OK;
   });
 }

@@ -132,6 +132,7 @@ struct OpTable {
   int nbox = 0;
   long long nrows = 0;
   bool direct = false;  // rows carry box-face reads (DRow::nbd / nbf)
+  int width = 0;        // widest box x-extent of the rows
   const DRow* rows() const { return d ? (const DRow*)d->p : nullptr; }
 };
 

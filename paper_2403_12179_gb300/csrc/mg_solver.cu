@@ -319,7 +319,7 @@ void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s,
       // (external records: captured into the step graph as event-record nodes)
       if (timed) MG_CK(cudaEventRecordWithFlags(H.sweep_ev[0], s, cudaEventRecordExternal));
       MG_CK(launch_rbgs_half(H.dt, D.smooth.rows(), D.smooth.nbox, D.smooth.nrows, color, s,
-                             D.direct, last ? last_norm : nullptr));
+                             D.direct, last ? last_norm : nullptr, D.smooth.width));
       if (timed) MG_CK(cudaEventRecordWithFlags(H.sweep_ev[1], s, cudaEventRecordExternal));
     }
 }
@@ -332,13 +332,15 @@ void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s, unsigned long long* no
     if (D.fused) launch_fill(c, *D.rhs, &H.bc, s, 1);  // rhs ghosts for the redundant ring
     smooth(c, H, D, H.p.nu1, s, nullptr, l == 0 && H.graph_timed);
     if (!D.direct) launch_fill(c, *D.phi, &H.bc, s, 1);
-    MG_CK(launch_residual_restrict(H.dt, D.rr.rows(), D.rr.nbox, D.rr.nrows, s, D.direct));
+    MG_CK(launch_residual_restrict(H.dt, D.rr.rows(), D.rr.nbox, D.rr.nrows, s, D.direct,
+                                   D.rr.width));
   }
   if (H.lc < nl) MG_CK(launch_coarse_cycle(H.dt, (const CoarseJob*)H.cjob->p, 1, H.csmem, s));
   else MG_CK(launch_bottom(H.dt, (const BottomJob*)H.job->p, 1, H.N, s));
   for (int l = top - 1; l >= 0; --l) {
     LevelData& D = H.L[l];
-    MG_CK(launch_prolong_add(H.dt, D.prolong.rows(), D.prolong.nbox, D.prolong.nrows, s));
+    MG_CK(launch_prolong_add(H.dt, D.prolong.rows(), D.prolong.nbox, D.prolong.nrows, s,
+                             D.prolong.width));
     smooth(c, H, D, H.p.nu2, s, l == 0 ? norm0 : nullptr);
   }
 }
