@@ -370,8 +370,9 @@ struct StepTimes {
   long long steps = 0;
 };
 
-void step_and_decide(Ctx& c, Staging& st, std::vector<Member*>& run, std::vector<Member*>& check,
-                     int nslots, cudaStream_t s, StepTimes* tm = nullptr) {
+void step_and_decide(Ctx& c, Staging& st, NormBuf& nb, std::vector<Member*>& run,
+                     std::vector<Member*>& check, int nslots, cudaStream_t s,
+                     StepTimes* tm = nullptr) {
   auto t0 = std::chrono::steady_clock::now();
   std::vector<Member*> fresh;
   for (Member* m : check)
@@ -384,10 +385,10 @@ void step_and_decide(Ctx& c, Staging& st, std::vector<Member*>& run, std::vector
   }
   upload_lists(c, S, st, s);
   auto t1 = std::chrono::steady_clock::now();
-  unsigned long long* norms = (unsigned long long*)c.d_norms->p;
+  unsigned long long* norms = (unsigned long long*)nb.d->p;
   const size_t nbytes = (size_t)nslots * 8;
   enqueue_step(c, S, (const unsigned char*)st.dev->p, norms, nbytes, !fresh.empty(), s);
-  MG_CK(cudaMemcpyAsync(c.h_norms, norms, nbytes, cudaMemcpyDeviceToHost, s));
+  MG_CK(cudaMemcpyAsync(nb.h, norms, nbytes, cudaMemcpyDeviceToHost, s));
   MG_CK(cudaStreamSynchronize(s));
   if (tm) {
     tm->plan += std::chrono::duration<double>(t1 - t0).count();
@@ -398,10 +399,10 @@ void step_and_decide(Ctx& c, Staging& st, std::vector<Member*>& run, std::vector
   for (Member* m : run) m->vcycles += 1;
   for (Member* m : check) {
     if (!m->started) {
-      m->rhsnorm = bits2d(c.h_norms[m->slot + 1]);
+      m->rhsnorm = bits2d(nb.h[m->slot + 1]);
       m->started = true;
     }
-    m->rn = bits2d(c.h_norms[m->slot]);
+    m->rn = bits2d(nb.h[m->slot]);
     decide(c, *m, s);
   }
   MG_CK(cudaStreamSynchronize(s));  // a zero-rhs member's phi reset completes before it retires
@@ -432,18 +433,19 @@ int solve_batch(Ctx& c, int n, const int64_t* rhs, const int64_t* phi, const mg_
     M[i].tol = tol;
     M[i].res.t_start = t0;
   }
-  c.ensure_norm_slots(2 * n);
+  NormBuf& nb = c.batch_norms;
+  nb.ensure(c, 2 * n, s);
   Staging st;
   std::vector<Member*> run, check;
   for (auto& m : M) check.push_back(&m);
-  step_and_decide(c, st, run, check, 2 * n, s);
+  step_and_decide(c, st, nb, run, check, 2 * n, s);
   for (;;) {
     run.clear();
     for (auto& m : M)
       if (!m.done) run.push_back(&m);
     if (run.empty()) break;
     check = run;
-    step_and_decide(c, st, run, check, 2 * n, s);
+    step_and_decide(c, st, nb, run, check, 2 * n, s);
   }
   int rc = MG_OK;
   for (int i = 0; i < n; ++i) {
@@ -477,6 +479,9 @@ struct Ctx::Server {
   size_t max_queue = 1 << 20;
   int max_active = 4096;
   mg_server_stats stats{};
+  // norm slots of the FP64 [0] and mixed-precision [1] members (separate: each group's
+  // check clears its whole array, and a mixed member's next step reads its last norm)
+  NormBuf norms[2];
 };
 
 
@@ -552,9 +557,9 @@ void server_loop(Ctx* c) {
       S.stats.max_active = std::max<int64_t>(S.stats.max_active, (int64_t)active.size());
     }
     try {
-      c->ensure_norm_slots(nslots);
       // one step per precision group: running members cycle, every member's norm is checked
       for (int dt : {DT_F64, DT_F32}) {
+        NormBuf& nb = S.norms[dt == DT_F64 ? 0 : 1];
         std::vector<Member*> run, check;
         for (auto& m : active) {
           if (m->done || m->H->dt != dt) continue;
@@ -563,7 +568,8 @@ void server_loop(Ctx* c) {
         }
         if (!check.empty()) {
           StepTimes tm;
-          step_and_decide(*c, st, run, check, nslots, s, &tm);
+          nb.ensure(*c, nslots, s);
+          step_and_decide(*c, st, nb, run, check, nslots, s, &tm);
           std::lock_guard<std::mutex> lk(S.mu);
           S.stats.plan_seconds += tm.plan;
           S.stats.step_seconds += tm.step;
@@ -610,6 +616,7 @@ void server_loop(Ctx* c) {
     }
   }
   if (st.dev) st.dev->reset(s);
+  for (NormBuf& nb : S.norms) nb.release(s);
   cudaStreamSynchronize(s);
 }
 

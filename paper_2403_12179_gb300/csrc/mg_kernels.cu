@@ -320,9 +320,12 @@ __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
 // except where a read is the cell's own value negated (a Dirichlet face): those cells sum
 // again, reading their new value.  (With an odd periodic extent an image could be the cell's
 // own colour; callers use this on even periodic extents only.)
+// Resident blocks per SM the half-sweep is built for (register budget): the norm variant
+// holds more live values.
+constexpr int kSweepMinBlocks = 4, kNormMinBlocks = 4;
 template <class T, bool DIRECT, bool NORM, int G>
-__global__ void __launch_bounds__(kThreads, 4) k_rbgs_half(SegList L, long long nrows, long long per,
-                                                        int color, unsigned long long* norms) {
+__global__ void __launch_bounds__(kThreads, NORM ? kNormMinBlocks : kSweepMinBlocks)
+    k_rbgs_half(SegList L, long long nrows, long long per, int color, unsigned long long* norms) {
   // A lane updates cells x and x + 2G of a pair step together (both of this colour: their
   // neighbours are of the other colour and unchanged, so both loads go first -- two
   // independent FP64 chains per lane).

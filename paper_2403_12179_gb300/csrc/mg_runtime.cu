@@ -100,18 +100,29 @@ int64_t Ctx::add_ba(std::shared_ptr<BoxArrayObj> b) {
   return id;
 }
 
-void Ctx::ensure_norm_slots(int n) {
-  if (n <= norm_slots) return;
-  int m = std::max(n, 64);
-  if (d_norms) {
-    MG_CK(cudaStreamSynchronize(stream));
-    d_norms.reset();
+void NormBuf::ensure(Ctx& c, int n, cudaStream_t s) {
+  if (n <= slots) return;
+  const int m = std::max(std::max(n, 64), 2 * slots);
+  DevBufP nd = c.alloc((size_t)m * 8, s);
+  MG_CK(cudaMemsetAsync(nd->p, 0, (size_t)m * 8, s));
+  if (d) MG_CK(cudaMemcpyAsync(nd->p, d->p, (size_t)slots * 8, cudaMemcpyDeviceToDevice, s));
+  unsigned long long* nh = nullptr;
+  MG_CK(cudaMallocHost(&nh, (size_t)m * 8));
+  MG_CK(cudaStreamSynchronize(s));
+  d = std::move(nd);
+  if (h) cudaFreeHost(h);
+  h = nh;
+  slots = m;
+}
+
+void NormBuf::release(cudaStream_t s) {
+  if (d) {
+    cudaStreamSynchronize(s);
+    d.reset();
   }
-  if (h_norms) cudaFreeHost(h_norms);
-  h_norms = nullptr;
-  d_norms = alloc((size_t)m * 8, stream);
-  MG_CK(cudaMallocHost(&h_norms, (size_t)m * 8));
-  norm_slots = m;
+  if (h) cudaFreeHost(h);
+  h = nullptr;
+  slots = 0;
 }
 
 void Ctx::load_tune_file() {
@@ -663,7 +674,8 @@ int mg_init(int device, size_t pool_bytes, mg_ctx_t* out) {
       size_t fr = 0, tot = 0;
       MG_CK(cudaMemGetInfo(&fr, &tot));
       c->pool_cap = pool_bytes ? pool_bytes : (size_t)(0.9 * (double)fr);
-      c->ensure_norm_slots(64);
+      c->batch_norms.ensure(*c, 64, c->stream);
+      c->op_norm.ensure(*c, 1, c->stream);
       c->d_err = c->alloc(256, c->stream);
       MG_CK(cudaMemsetAsync(c->d_err->p, 0, 256, c->stream));
       MG_CK(cudaStreamSynchronize(c->stream));
@@ -688,11 +700,11 @@ int mg_finalize(mg_ctx_t h) {
     c->fabs.clear();
     c->tag_cache.clear();
     c->bas.clear();
-    c->d_norms.reset();
+    c->batch_norms.release(c->stream);
+    c->op_norm.release(c->stream);
     c->d_err.reset();
     if (c->device >= 0) {
       cudaStreamSynchronize(c->stream);
-      if (c->h_norms) cudaFreeHost(c->h_norms);
       cudaDeviceSynchronize();
       if (c->pool) cudaMemPoolDestroy(c->pool);
       if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -1163,13 +1175,14 @@ int mg_residual(mg_ctx_t h, mg_fab_t phi, mg_fab_t rhs, mg_fab_t r, double hh, d
         if (fo) R.v[2] = fo->view(b);
       }, c->stream);
     });
-    unsigned long long* dn = (unsigned long long*)c->d_norms->p;
+    std::lock_guard<std::mutex> nl(c->op_norm_mu);
+    unsigned long long* dn = (unsigned long long*)c->op_norm.d->p;
     MG_CK(cudaMemsetAsync(dn, 0, 8, s));
     MG_CK(launch_residual(fp->dtype, t.rows(), t.nbox, t.nrows, dn, s));
     if (norm) {
-      MG_CK(cudaMemcpyAsync(c->h_norms, dn, 8, cudaMemcpyDeviceToHost, s));
+      MG_CK(cudaMemcpyAsync(c->op_norm.h, dn, 8, cudaMemcpyDeviceToHost, s));
       MG_CK(cudaStreamSynchronize(s));
-      std::memcpy(norm, c->h_norms, 8);
+      std::memcpy(norm, c->op_norm.h, 8);
     }
     return MG_OK;
   });

@@ -66,6 +66,19 @@ struct DevBuf {
 };
 using DevBufP = std::unique_ptr<DevBuf>;
 
+struct Ctx;
+
+// Norm slots of batched steps: a device array of max-norm bit patterns and its pinned host
+// mirror.  Growing keeps the device values: a mixed-precision member's next step scales its
+// residual by the norm its last check left there.
+struct NormBuf {
+  DevBufP d;
+  unsigned long long* h = nullptr;
+  int slots = 0;
+  void ensure(Ctx& c, int n, cudaStream_t s);  // at least n slots (new slots zero)
+  void release(cudaStream_t s);
+};
+
 struct BoxArrayObj {
   BoxArray ba;
   bool levels_built = false;
@@ -167,10 +180,10 @@ struct Ctx {
   std::map<std::string, std::vector<double>> bottom_cache;  // key -> transposed M
   // device error word written by kernels whose bounded waits expire (0 = fine)
   DevBufP d_err;
-  // scratch for norms (device) and its pinned host mirror
-  DevBufP d_norms;
-  unsigned long long* h_norms = nullptr;
-  int norm_slots = 0;
+  // norm slots of mg_solve_batch, and the one norm of the level-operation entry points
+  // (the serving scheduler keeps its own, one set per precision)
+  NormBuf batch_norms, op_norm;
+  std::mutex op_norm_mu;
   // cached stencil tables of the level-operation entry points, keyed by op, fabs and h
   struct CachedOp {
     std::vector<int64_t> fabs;
@@ -203,7 +216,6 @@ struct Ctx {
   std::shared_ptr<BoxArrayObj> get_ba(int64_t id);
   std::shared_ptr<FabObj> get_fab(int64_t id);
   int64_t add_ba(std::shared_ptr<BoxArrayObj> b);
-  void ensure_norm_slots(int n);
 };
 
 int bc_code(const mg_bc* bc, int periodic[3]);  // validates; returns a small cache key

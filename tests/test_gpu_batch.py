@@ -1,6 +1,8 @@
 """Batched solves (one launch per V-cycle stage for many solves) and the serving loop
 (continuous batching via mg_submit / mg_poll): every result must equal, bit for bit, the
 same problem solved alone with mg_solve, whatever company it had."""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -102,6 +104,38 @@ def test_serving_results_equal_alone(precision):
             phi = gu.fab_dense(ctx, fp, rhs.shape)
             phi_a, res_a = _alone(actx, n, b, p, 200 + i, precision)
             assert res_a.vcycles == r.vcycles
+            assert np.array_equal(phi, phi_a)
+    finally:
+        mg.mg_finalize(ctx)
+        mg.mg_finalize(actx)
+
+
+def test_serving_many_members_both_precisions_equal_alone():
+    """More members than the initial norm slots hold (the arrays grow while members run),
+    FP64 and mixed-precision members at once, later requests joining running ones: every
+    result and V-cycle count equals the solve alone."""
+    ctx = mg.mg_init(0)
+    actx = mg.mg_init(0)
+    try:
+        count = 84
+        specs = [PROBLEMS[i % len(PROBLEMS)] for i in range(count)]
+        precs = [mg.MG_PREC_F64 if i % 3 == 0 else mg.MG_PREC_MIXED for i in range(count)]
+        made, tickets = [], []
+        for i, ((n, b, p), pr) in enumerate(zip(specs, precs)):
+            m = _make(ctx, n, b, p, 400 + i)
+            made.append(m)
+            tickets.append(mg.mg_submit(ctx, m[1], m[2], mg.make_bc(p), 1e-10,
+                                        mg.make_options(precision=pr)))
+            if i % 12 == 11:
+                time.sleep(0.02)
+        res = [mg.mg_poll(ctx, t, -1)[1] for t in tickets]
+        stats = mg.mg_server_stats_get(ctx)
+        assert stats["completed"] == count
+        for i, ((n, b, p), pr, (rhs, fr, fp), r) in enumerate(zip(specs, precs, made, res)):
+            assert r.status == mg.MG_OK and r.rel_resid <= 1e-10
+            phi = gu.fab_dense(ctx, fp, rhs.shape)
+            phi_a, res_a = _alone(actx, n, b, p, 400 + i, pr)
+            assert res_a.vcycles == r.vcycles, (i, n, b, p, pr)
             assert np.array_equal(phi, phi_a)
     finally:
         mg.mg_finalize(ctx)
