@@ -90,7 +90,7 @@ struct UnitB {
   std::vector<UnitSeg> v;
   long long total = 0;
   size_t off = 0;
-  int ty = 1, depth = 3, mp = 0, mpr = 0;
+  int ty = 1, depth = 4, mp = 0, mpr = 0;
   bool rhs_smem = true;
   void add(const FusedTable& t) {
     UnitSeg s{};

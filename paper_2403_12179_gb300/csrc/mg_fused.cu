@@ -395,10 +395,11 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
       }
     }
     // red ring cells x = -1 and x = nx of rows inside the box (their red value feeds the
-    // black update of x = 0 / nx-1 in the next stage), one thread per row
+    // black update of x = 0 / nx-1 in the next stage), one thread per row, counted from the
+    // last consumer down (the first warps take the rows past a full pass above)
     if (red && !ghost_plane) {
       const bool lo_in = !(S.flags & 1), hi_in = !(S.flags & 8);
-      for (int y = ya + tid; y <= yb; y += kConsumers) {
+      for (int y = ya + (kConsumers - 1 - tid); y <= yb; y += kConsumers) {
         if (y < 0 || y >= S.ny) continue;
         const int gy = S.loy + y;
         const int orow = (y - S.y0 + 2) * S.pitch + S.g;
@@ -465,7 +466,8 @@ static cudaError_t launch_fused_d(const UnitList& L, long long nunits, int ty, i
                                   int max_pitch, int max_pitch_r, int* err, cudaStream_t s) {
   if (depth <= 1) return launch_fused_t<T, 1, RS>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
   if (depth == 2) return launch_fused_t<T, 2, RS>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
-  return launch_fused_t<T, 3, RS>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+  if (depth == 3) return launch_fused_t<T, 3, RS>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
+  return launch_fused_t<T, 4, RS>(L, nunits, ty, max_pitch, max_pitch_r, err, s);
 }
 
 cudaError_t launch_rbgs_fused_l(int dt, const UnitList& L, long long nunits, int ty, int depth,

@@ -136,7 +136,7 @@ void Ctx::load_tune_file() {
   while (std::fgets(line, sizeof line, f)) {
     FusedCfg cfg;
     if (std::sscanf(line, "%199s %d %d %d %d", key, &cfg.ty, &cfg.zc, &cfg.depth, &cfg.rhs_smem) == 5 &&
-        cfg.ty > 0 && cfg.zc > 0 && cfg.depth >= 1 && cfg.depth <= 3)
+        cfg.ty > 0 && cfg.zc > 0 && cfg.depth >= 1 && cfg.depth <= 4)
       tune[key] = cfg;
   }
   std::fclose(f);
@@ -465,8 +465,10 @@ FusedTable make_fused(Ctx& c, const BoxArray& ba, double h, const FabObj& src, c
   MG_CK(cudaEventCreate(&e0));
   MG_CK(cudaEventCreate(&e1));
   for (int rs : {1, 0})
-  for (int depth : {2, 3})
-    for (int ty : {4, 8, 16, 32}) {
+  for (int depth : {2, 3, 4})
+    // tile rows: powers of two, and ty + 2 (the rows of a red pass with its ring) a
+    // multiple of 8 or 16 (the rows the consumers cover in one pass for wide boxes)
+    for (int ty : {4, 6, 8, 14, 16, 22, 30, 32}) {
       if (ty > 2 * mx[1] && ty != 4) continue;
       for (int zc : {8, 16, 32, 64}) {
         if (zc > 2 * mx[2] && zc != 8) continue;
