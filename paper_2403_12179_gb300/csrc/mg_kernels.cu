@@ -14,6 +14,7 @@
 #include <atomic>
 #include <cstdio>
 
+#include "mg_bits.hpp"
 #include "mg_kernels.hpp"
 
 namespace gbmg {
@@ -593,54 +594,77 @@ __global__ void __launch_bounds__(kThreads) k_maxabs(SegList L, long long nrows,
 __device__ __forceinline__ double norm_of(const unsigned long long* norms, int idx) {
   return __longlong_as_double((long long)norms[idx]);
 }
-// 2^e with 2^e <= s < 2^(e+1), and its inverse; both exact powers of two
-__device__ __forceinline__ double pow2_floor(double s) { return ldexp(1.0, ilogb(s)); }
-__device__ __forceinline__ double pow2_floor_inv(double s) { return ldexp(1.0, -ilogb(s)); }
+// 2^e with 2^e <= s < 2^(e+1), and its inverse; both exact powers of two (bit operations)
+__device__ __forceinline__ double pow2_floor(double s) { return bits::pow2(bits::floor_log2(s)); }
+__device__ __forceinline__ double pow2_floor_inv(double s) { return bits::pow2(-bits::floor_log2(s)); }
 
 // r32 = float(r * 2^-e) with 2^e <= ||r||_inf < 2^(e+1), from the FP64 residual stored by the
 // preceding norm check (the same values the norm was taken over), and the FP32 correction's
-// initial guess e32 = 0.
+// initial guess e32 = 0.  G lanes per x-line, four cells per lane step, loads first.
+template <int G>
 __global__ void __launch_bounds__(kThreads) k_scale_residual_f32(SegList L, long long nrows,
                                                                  long long per,
                                                                  const unsigned long long* norms) {
-  const int lane = threadIdx.x & 31;
-  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
+  const int sub = threadIdx.x & (G - 1);
+  for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)lr % n1, z = (int)lr / n1;
     const double* __restrict__ r = line<double>(R.v[0], y, z);
     float* __restrict__ r32 = line<float>(R.c[0], y, z);
     float* __restrict__ e32 = line<float>(R.c[1], y, z);
-    const double down = pow2_floor_inv(norm_of(norms, slot + R.solve));
-    for (int x = lane; x < n0; x += 32) {
-      r32[x] = __double2float_rn(__dmul_rn(__ldg(r + x), down));
-      e32[x] = 0.0f;
+    const double s = norm_of(norms, slot + R.solve);
+    const int e = bits::floor_log2(s);
+    const double down = pow2_floor_inv(s);
+    for (int x = sub; x < n0; x += 4 * G) {
+      double v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (x + G * k < n0) v[k] = __ldg(r + x + G * k);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (x + G * k >= n0) continue;
+        // the exact scaling and the rounding in integer operations where they apply
+        float f;
+        if (!bits::scale_to_f32(v[k], e, &f)) f = __double2float_rn(__dmul_rn(v[k], down));
+        r32[x + G * k] = f;
+        e32[x + G * k] = 0.0f;
+      }
     }
   });
 }
 
-// phi += 2^e * e32 (FP64 fma); each lane loads all its cells of a row before storing.
+// phi += 2^e * e32 (one rounding).  2^e * e32 is exact in binary64 (a float times a power of
+// two), so where the bit form applies one rounded addition gives the fma's result.  G lanes
+// per x-line, four cells per lane step, loads first.
+template <int G>
 __global__ void __launch_bounds__(kThreads) k_correct_add(SegList L, long long nrows, long long per,
                                                           const unsigned long long* norms) {
-  const int lane = threadIdx.x & 31;
-  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
+  const int sub = threadIdx.x & (G - 1);
+  for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
     const int n0 = R.n[0], n1 = R.n[1];
     const int y = (int)lr % n1, z = (int)lr / n1;
     double* __restrict__ phi = line<double>(R.v[0], y, z);
     const float* __restrict__ e = line<float>(R.c[0], y, z);
-    const double up = pow2_floor(norm_of(norms, slot + R.solve));
-    int x = lane;
-    for (; x + 96 < n0; x += 128) {
+    const double s = norm_of(norms, slot + R.solve);
+    const int ex = bits::floor_log2(s);
+    const double up = pow2_floor(s);
+    for (int x = sub; x < n0; x += 4 * G) {
       double p[4];
       float v[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        p[k] = phi[x + 32 * k];
-        v[k] = __ldg(e + x + 32 * k);
-      }
+      for (int k = 0; k < 4; ++k)
+        if (x + G * k < n0) {
+          p[k] = phi[x + G * k];
+          v[k] = __ldg(e + x + G * k);
+        }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) phi[x + 32 * k] = __fma_rn(up, (double)v[k], p[k]);
+      for (int k = 0; k < 4; ++k) {
+        if (x + G * k >= n0) continue;
+        double t;
+        phi[x + G * k] = bits::scaled_f32_to_f64(v[k], ex, &t) ? __dadd_rn(p[k], t)
+                                                               : __fma_rn(up, (double)v[k], p[k]);
+      }
     }
-    for (; x < n0; x += 32) phi[x] = __fma_rn(up, (double)__ldg(e + x), phi[x]);
   });
 }
 
@@ -842,8 +866,11 @@ cudaError_t launch_maxabs_l(int dt, const SegList& L, long long nrows, unsigned 
 cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,
                                         const unsigned long long* norms, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 16);
-  k_scale_residual_f32<<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
+  const int G = group_lanes(L.width, 4, 8, 32);  // four cells per lane
+  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  if (G == 32) k_scale_residual_f32<32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
+  else if (G == 16) k_scale_residual_f32<16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
+  else k_scale_residual_f32<8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -851,8 +878,11 @@ cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,
 cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsigned long long* norms,
                                  cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
-  Grid g = row_grid(nrows, 16);
-  k_correct_add<<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
+  const int G = group_lanes(L.width, 4, 8, 32);
+  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  if (G == 32) k_correct_add<32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
+  else if (G == 16) k_correct_add<16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
+  else k_correct_add<8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -934,13 +964,13 @@ cudaError_t launch_maxabs(int dt, const DRow* rows, int nbox, long long nrows,
 }
 
 cudaError_t launch_scale_residual_f32(const DRow* rows, int nbox, long long nrows,
-                                      const unsigned long long* norms, cudaStream_t s) {
-  return launch_scale_residual_f32_l(one_seg(rows, nbox), nrows, norms, s);
+                                      const unsigned long long* norms, cudaStream_t s, int width) {
+  return launch_scale_residual_f32_l(one_seg(rows, nbox, 0, width), nrows, norms, s);
 }
 
 cudaError_t launch_correct_add(const DRow* rows, int nbox, long long nrows,
-                               const unsigned long long* norms, cudaStream_t s) {
-  return launch_correct_add_l(one_seg(rows, nbox), nrows, norms, s);
+                               const unsigned long long* norms, cudaStream_t s, int width) {
+  return launch_correct_add_l(one_seg(rows, nbox, 0, width), nrows, norms, s);
 }
 
 }  // namespace gbmg

@@ -243,10 +243,12 @@ cudaError_t launch_maxabs(int dt, const DRow* rows, int nbox, long long nrows,
 // c[1] = e32 out (FP32 views with the same box geometry): r32 = float(r * 2^-e) with
 // 2^e <= norms[solve] < 2^(e+1), e32 = 0.
 cudaError_t launch_scale_residual_f32(const DRow* rows, int nbox, long long nrows,
-                                      const unsigned long long* norms, cudaStream_t s);
-// v[0] = phi (FP64), c[0] = e (FP32 view, same geometry): phi = phi + s * double(e).
+                                      const unsigned long long* norms, cudaStream_t s,
+                                      int width = 0);
+// v[0] = phi (FP64), c[0] = e (FP32 view, same geometry): phi = phi + 2^e * double(e32) with
+// the 2^e of the scale above.
 cudaError_t launch_correct_add(const DRow* rows, int nbox, long long nrows,
-                               const unsigned long long* norms, cudaStream_t s);
+                               const unsigned long long* norms, cudaStream_t s, int width = 0);
 
 // Launchers over segment lists (several solves per launch); nrows / nchunks / nunits are
 // the totals over all segments.

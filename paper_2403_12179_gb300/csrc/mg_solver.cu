@@ -350,7 +350,8 @@ void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s, unsigned long long* no
 void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
   unsigned long long* dn = (unsigned long long*)H.dnorm->p;
   if (H.mixed)  // the FP32 right-hand side from the residual of the last norm check; e = 0
-    MG_CK(launch_scale_residual_f32(H.scale0.rows(), H.scale0.nbox, H.scale0.nrows, dn, s));
+    MG_CK(launch_scale_residual_f32(H.scale0.rows(), H.scale0.nbox, H.scale0.nrows, dn, s,
+                                    H.scale0.width));
   // FP64 with half-sweeps on the finest level: the cycle's last (black) half-sweep there
   // takes the residual norm of the cells it updates, and only the red cells need a residual
   // pass; the values are those of a full residual pass
@@ -365,7 +366,8 @@ void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
   if (split_norm) MG_CK(cudaMemsetAsync(dn, 0, 8, s));
   enqueue_vcycle(c, H, s, split_norm ? dn : nullptr);
   if (H.mixed)
-    MG_CK(launch_correct_add(H.correct0.rows(), H.correct0.nbox, H.correct0.nrows, dn, s));
+    MG_CK(launch_correct_add(H.correct0.rows(), H.correct0.nbox, H.correct0.nrows, dn, s,
+                             H.correct0.width));
   if (!split_norm) MG_CK(cudaMemsetAsync(dn, 0, 8, s));
   if (!H.direct0) launch_fill(c, *H.phi0, &H.bc, s, 1);
   MG_CK(launch_residual(DT_F64, H.resid0.rows(), H.resid0.nbox, H.resid0.nrows, dn, s, H.direct0,
