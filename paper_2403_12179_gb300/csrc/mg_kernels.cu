@@ -68,6 +68,19 @@ __device__ __forceinline__ T residual_of(T s, T phi, T rhs, T ih2) {
   return Ar<T>::fma(Ar<T>::neg(ih2), Ar<T>::fma(T(-6), phi, s), rhs);
 }
 
+// A level constant (h^2, 1/h^2; binary64 in the box table) in the kernel's type.  For binary32
+// the rounding is done with integer operations: a conversion would occupy the FP64 pipe once per
+// row and lane of an otherwise FP32 kernel.
+template <class T>
+__device__ __forceinline__ T level_const(double d);
+template <>
+__device__ __forceinline__ double level_const<double>(double d) { return d; }
+template <>
+__device__ __forceinline__ float level_const<float>(double d) {
+  float f;
+  return bits::scale_to_f32(d, 0, &f) ? f : __double2float_rn(d);
+}
+
 constexpr int kWarps = 8;  // warps per block in the row kernels
 constexpr int kThreads = kWarps * 32;
 
@@ -338,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, NORM ? kNormMinBlocks : kSweepMinBlo
     const int y = (int)lr % n1, z = (int)lr / n1;
     T* phi = line<T>(R.v[0], y, z);
     const T* rhs = line<T>(R.v[1], y, z);
-    const T h2 = (T)R.h2, ih2 = (T)R.ih2;
+    const T h2 = level_const<T>(R.h2), ih2 = level_const<T>(R.ih2);
     const int par = (color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1;
     cur = slot + R.solve;
     auto norm = [&](T s, T u, T r) {
@@ -404,7 +417,7 @@ __global__ void __launch_bounds__(kThreads, DIRECT ? 4 : 6) k_residual(SegList L
     const T* phi = line<T>(R.v[0], y, z);
     const T* rhs = line<T>(R.v[1], y, z);
     T* r = R.v[2].p ? line<T>(R.v[2], y, z) : nullptr;
-    const T ih2 = (T)R.ih2;
+    const T ih2 = level_const<T>(R.ih2);
     const Nbr<T> nb = DIRECT ? nbr_rows<T>(R, phi, y, z) : Nbr<T>{};
     auto cell = [&](int x, T s) {
       T v = residual_of(s, phi[x], rhs[x], ih2);
@@ -439,7 +452,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_restrict(SegList L, long 
     const int nc0 = R.n[0] >> 1, nc1 = R.n[1] >> 1;
     const int Y = (int)lr % nc1, Z = (int)lr / nc1;
     const DView vp = R.v[0], vr = R.v[1];
-    const T ih2 = (T)R.ih2;
+    const T ih2 = level_const<T>(R.ih2);
     T* crhs = line<T>(R.c[0], Y, Z);
     T* cphi = R.c[1].p ? line<T>(R.c[1], Y, Z) : nullptr;
     const int n0 = R.n[0];
