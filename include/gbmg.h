@@ -73,7 +73,11 @@ typedef struct {
   int nu2;            /* post-smoothing sweeps, default 2 */
   int max_iter;       /* V-cycle limit, default 50 */
   int precision;      /* MG_PREC_F64 (default) or MG_PREC_MIXED */
-  int smoother;       /* MG_SMOOTH_AUTO (default), _HALF or _FUSED */
+  int smoother;       /* MG_SMOOTH_AUTO (default): the fused red + black sweep on FP32 levels
+                         of at least 256^3 cells, half-sweeps elsewhere; _HALF: half-sweeps
+                         everywhere; _FUSED: the fused sweep on every level but the bottom
+                         (the caller's FP64 level 0 then needs phi nghost >= 2, rhs >= 1).
+                         All three give the same results. */
   int use_graph;      /* 1 (default): replay each V-cycle as a CUDA graph */
   int fixed_vcycles;  /* >= 0: run exactly this many V-cycles, no stop test; -1 default */
   double h;           /* cell size; 0 (default) means 1 / (domain x extent) */
