@@ -8,7 +8,14 @@ solve (phi reset to 0, then mg_solve) with rhs already resident in HBM.  `value`
 over all ranks (each rank solves its own replica: this solve is not sharded across GPUs).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload dirichlet256|periodic64|mixed512]
+                    [--workload dirichlet256|periodic64|mixed512|batched512|serving|fill]
+                    [--kernels-only] [--no-cpu-baseline]
+
+Other workloads: mixed512 (512^3, FP32 inner / FP64 outer, against the FP64 solve),
+batched512 (512 independent solves packed into shared launches), serving (5000 Poisson
+arrivals through mg_submit/mg_poll, with latency percentiles and capacity, against a
+one-solve-at-a-time FP64 server), fill (the ghost-fill microbench, fused against one launch
+per copy tag).
 
 `--impl reference` times the CPU oracle (the plain FP64 restatement under oracle/) on this
 machine's host cores on the same workload, one V-cycle per step, extrapolated to a solve.
