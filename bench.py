@@ -116,15 +116,19 @@ class Clocks:
 
 # ---- distributed plumbing ----------------------------------------------------------------
 
-def dist_init(args):
+def dist_init(args, backend=None):
+    """One process per GPU (torchrun's RANK / WORLD_SIZE / LOCAL_RANK); NCCL on GPUs, gloo
+    where there is none (the host-side tests)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        backend = backend or ("nccl" if torch.cuda.is_available() else "gloo")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return rank, world, local
 
 
@@ -139,9 +143,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(world, steps, max_total_ms):
+    """Units per second over all ranks: every rank processed `steps` units, and the slowest
+    rank's timed region (max over ranks) took max_total_ms."""
+    return world * steps / (max_total_ms / 1e3)
 
 
 # ---- our arm --------------------------------------------------------------------------------
@@ -244,7 +255,7 @@ def run_ours(args, wl_name):
     per = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
     total_ms = max_over_ranks(sum(per), world)
     del flush
-    value = world * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(world, args.steps, total_ms)
     vcycles = results[-1].vcycles
     assert all(r.status == 0 and r.rel_resid <= 1e-10 for r in results)
 
