@@ -232,8 +232,9 @@ def restrict(fine_level, fine, ng_f, coarse_level, ng_c):
     return unpack(fc, coarse)
 
 
-def prolong_add(coarse_level, coarse, ng_c, fine_level, fine, ng_f):
-    """fine + piecewise-constant injection of coarse (valid cells)."""
+def prolong_add(coarse_level, coarse, ng_c, fine_level, fine, ng_f, trilinear=False):
+    """fine + piecewise-constant injection of coarse (valid cells); trilinear: the trilinear
+    form, which reads coarse's ghosts as they are (fill them first)."""
     lib = _load()
     fdlo, fdhi, fb = fine_level
     cdlo, cdhi, cb = coarse_level
@@ -241,7 +242,8 @@ def prolong_add(coarse_level, coarse, ng_c, fine_level, fine, ng_f):
     fc, ff = pack(coarse), pack(fine)
     rc = lib.orc_prolong(_ip(_i3(cdlo)), _ip(_i3(cdhi)), ctypes.c_int(len(cb)), _ip(cb),
                          ctypes.c_int(ng_c), _dp(fc), _ip(_i3(fdlo)), _ip(_i3(fdhi)),
-                         ctypes.c_int(len(fb)), _ip(fb), ctypes.c_int(ng_f), _dp(ff))
+                         ctypes.c_int(len(fb)), _ip(fb), ctypes.c_int(ng_f), _dp(ff),
+                         ctypes.c_int(1 if trilinear else 0))
     if rc != OK:
         raise ValueError(f"orc_prolong failed ({rc})")
     return unpack(ff, fine)
@@ -260,8 +262,9 @@ def bottom_matrix(n, periodic, h):
 
 
 def solve(dlo, dhi, periodic, boxes, h, rhs, phi0=None, tol=1e-10, max_iter=50, nu1=2, nu2=2,
-          fixed_vcycles=-1, mixed=False):
-    """V-cycle solve of A phi = rhs on a dense domain array (nz, ny, nx).
+          fixed_vcycles=-1, mixed=False, trilinear=False):
+    """V-cycle solve of A phi = rhs on a dense domain array (nz, ny, nx); trilinear selects
+    the trilinear prolongation.
 
     Returns (phi, status, vcycles, hist) where hist[i] is ||rhs - A phi_i||_inf / ||rhs||_inf
     before V-cycle i (and after the last one)."""
@@ -275,7 +278,8 @@ def solve(dlo, dhi, periodic, boxes, h, rhs, phi0=None, tol=1e-10, max_iter=50, 
                        _ip(boxes), ctypes.c_double(h), _dp(rhs), _dp(phi), ctypes.c_double(tol),
                        ctypes.c_int(max_iter), ctypes.c_int(nu1), ctypes.c_int(nu2),
                        ctypes.c_int(fixed_vcycles), ctypes.c_int(1 if mixed else 0),
-                       ctypes.byref(vc), _dp(hist), ctypes.c_int(len(hist)))
+                       ctypes.byref(vc), _dp(hist), ctypes.c_int(len(hist)),
+                       ctypes.c_int(1 if trilinear else 0))
     if rc == EINVAL:
         raise ValueError("orc_solve: invalid problem")
     return phi, rc, vc.value, hist[:vc.value + 1].copy()

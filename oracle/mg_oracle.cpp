@@ -18,7 +18,9 @@
 //       - residual r = fma(-1/h^2, fma(-6, phi, s), rhs), max-norm
 //       - restriction = mean of the 8 children (x fastest sum order), coarse guess 0,
 //         coarse operator rediscretised with h_{l+1} = 2 h_l
-//       - prolongation = piecewise-constant injection added to phi
+//       - prolongation = piecewise-constant injection added to phi (default), or trilinear:
+//         weights 3/4 (parent) and 1/4 (its neighbour towards the fine cell) per dimension,
+//         applied x, then y, then z, each step fma(1/4, b, 3/4 * a), from filled coarse ghosts
 //       - bottom = exact solve by the closed-form (pseudo-)inverse built from the discrete
 //         sine / Fourier eigenvectors of the 1-D operators
 //       - V(nu1, nu2) cycle, stop when ||rhs - A phi||_inf <= tol ||rhs||_inf
@@ -283,6 +285,38 @@ void prolong_add(const Field<R>& coarse, const Field<R>& fine) {
   }
 }
 
+// Trilinear prolongation: phi_fine(c) += e(c), where e interpolates the coarse correction
+// linearly in each dimension between the parent P (weight 3/4) and P's neighbour on c's side
+// (weight 1/4) -- the cell-centred linear interpolation, fine centres lying a quarter of a
+// coarse cell from P's centre.  Dimension by dimension, x then y then z, each step
+// lerp(a, b) = fma(1/4, b, 3/4 * a).  Reads the coarse ghosts as they are (fill first).
+template <class R>
+R lerp34(R a, R b) { return std::fma((R)0.25, b, (R)0.75 * a); }
+
+template <class R>
+void prolong_add_trilinear(const Field<R>& coarse, const Field<R>& fine) {
+  const Level& F = *fine.L;
+  const Level& C = *coarse.L;
+#pragma omp parallel for schedule(dynamic)
+  for (long long b = 0; b < (long long)F.boxes.size(); ++b) {
+    const Box& B = F.boxes[b];
+    for (int z = B.lo[2]; z <= B.hi[2]; ++z)
+      for (int y = B.lo[1]; y <= B.hi[1]; ++y)
+        for (int x = B.lo[0]; x <= B.hi[0]; ++x) {
+          const int X = floordiv2(x), Y = floordiv2(y), Z = floordiv2(z);
+          const int sx = (x - 2 * X) ? 1 : -1, sy = (y - 2 * Y) ? 1 : -1, sz = (z - 2 * Z) ? 1 : -1;
+          const int o = C.owner[dom_index(C, X, Y, Z)];
+          auto v = [&](int i, int j, int k) { return coarse.at(o, X + i * sx, Y + j * sy, Z + k * sz); };
+          const R ux00 = lerp34(v(0, 0, 0), v(1, 0, 0));
+          const R ux10 = lerp34(v(0, 1, 0), v(1, 1, 0));
+          const R ux01 = lerp34(v(0, 0, 1), v(1, 0, 1));
+          const R ux11 = lerp34(v(0, 1, 1), v(1, 1, 1));
+          const R u = lerp34(lerp34(ux00, ux10), lerp34(ux01, ux11));
+          fine.at((int)b, x, y, z) = fine.at((int)b, x, y, z) + u;
+        }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Bottom solve.  The 1-D operators (u_{i-1} - 2u_i + u_{i+1})/h^2 with either periodic or
 // reflecting (ghost = -mirror) ends have known orthonormal eigenvectors:
@@ -512,7 +546,7 @@ void smooth(const Field<R>& phi, const Field<R>& rhs, int nsweeps) {
 
 template <class R>
 void vcycle(std::vector<LevelData<R>>& D, const std::vector<std::vector<double>>& Mb, size_t l,
-            int nu1, int nu2) {
+            int nu1, int nu2, bool trilinear) {
   size_t bottom = D.size() - 1;
   if (l == bottom) {
     bottom_apply(Mb[0], D[l].frhs, D[l].fphi);
@@ -523,8 +557,13 @@ void vcycle(std::vector<LevelData<R>>& D, const std::vector<std::vector<double>>
   residual(D[l].fphi, D[l].frhs, &D[l].fr);
   restrict_avg(D[l].fr, D[l + 1].frhs);
   zero_valid(D[l + 1].fphi);
-  vcycle(D, Mb, l + 1, nu1, nu2);
-  prolong_add(D[l + 1].fphi, D[l].fphi);
+  vcycle(D, Mb, l + 1, nu1, nu2, trilinear);
+  if (trilinear) {
+    fill(D[l + 1].fphi);
+    prolong_add_trilinear(D[l + 1].fphi, D[l].fphi);
+  } else {
+    prolong_add(D[l + 1].fphi, D[l].fphi);
+  }
   smooth(D[l].fphi, D[l].frhs, nu2);
 }
 
@@ -683,16 +722,22 @@ int orc_restrict(const int fdlo[3], const int fdhi[3], int fnbox, const int* flo
   return ORC_OK;
 }
 
+// trilinear != 0: the trilinear form, reading the coarse ghosts as they are (fill first).
 int orc_prolong(const int cdlo[3], const int cdhi[3], int cnbox, const int* clohi, int ng_c,
                 const double* coarse, const int fdlo[3], const int fdhi[3], int fnbox,
-                const int* flohi, int ng_f, double* fine) {
+                const int* flohi, int ng_f, double* fine, int trilinear) {
   int per[3] = {0, 0, 0};
   Level F = make_level(fdlo, fdhi, per, 1.0, fnbox, flohi);
   Level C = make_level(cdlo, cdhi, per, 2.0, cnbox, clohi);
   if (!build_owner(F) || !build_owner(C)) return ORC_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (2 * C.dlo[d] != F.dlo[d] || 2 * C.dhi[d] + 1 != F.dhi[d]) return ORC_EINVAL;
-  prolong_add(make_field(C, ng_c, 1, const_cast<double*>(coarse)), make_field(F, ng_f, 1, fine));
+  if (trilinear) {
+    if (ng_c < 1) return ORC_EINVAL;
+    prolong_add_trilinear(make_field(C, ng_c, 1, const_cast<double*>(coarse)), make_field(F, ng_f, 1, fine));
+  } else {
+    prolong_add(make_field(C, ng_c, 1, const_cast<double*>(coarse)), make_field(F, ng_f, 1, fine));
+  }
   return ORC_OK;
 }
 
@@ -707,10 +752,12 @@ int orc_bottom_matrix(const int n[3], const int periodic[3], double h, double* M
 // on entry and the result on exit.  fixed_vcycles >= 0 runs exactly that many V-cycles with
 // no stop test.  mixed != 0 selects the FP64-outer / FP32-inner form.  hist receives the
 // relative residual before each V-cycle and after the last (hist_cap entries at most).
+// trilinear != 0 selects the trilinear prolongation.
 // Returns ORC_OK, ORC_NOT_CONVERGED, ORC_ENAN or ORC_EINVAL.
 int orc_solve(const int dlo[3], const int dhi[3], const int periodic[3], int nbox, const int* lohi,
               double h, const double* rhs_g, double* phi_g, double tol, int max_iter, int nu1,
-              int nu2, int fixed_vcycles, int mixed, int* vcycles, double* hist, int hist_cap) {
+              int nu2, int fixed_vcycles, int mixed, int* vcycles, double* hist, int hist_cap,
+              int trilinear) {
   Level L0 = make_level(dlo, dhi, periodic, h, nbox, lohi);
   std::vector<Level> levels;
   if (!build_hierarchy(L0, levels)) return ORC_EINVAL;
@@ -750,7 +797,7 @@ int orc_solve(const int dlo[3], const int dhi[3], const int periodic[3], int nbo
       if (it == max_iter) { status = ORC_NOT_CONVERGED; break; }
     }
     if (!mixed) {
-      vcycle(D, Mb, 0, nu1, nu2);
+      vcycle(D, Mb, 0, nu1, nu2, trilinear != 0);
     } else {
       // Inner FP32 V-cycle on the residual scaled by 2^-e, 2^e <= ||r|| < 2^(e+1) (exact),
       // FP64 correction add.
@@ -765,7 +812,7 @@ int orc_solve(const int dlo[3], const int dhi[3], const int periodic[3], int nbo
               Df[0].frhs.at((int)b, x, y, z) = (float)(D[0].fr.at((int)b, x, y, z) * down);
       }
       zero_valid(Df[0].fphi);
-      vcycle(Df, Mb, 0, nu1, nu2);
+      vcycle(Df, Mb, 0, nu1, nu2, trilinear != 0);
       for (size_t b = 0; b < L.boxes.size(); ++b) {
         const Box& B = L.boxes[b];
         for (int z = B.lo[2]; z <= B.hi[2]; ++z)
