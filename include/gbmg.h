@@ -58,6 +58,7 @@ enum { MG_BC_PERIODIC = 0, MG_BC_DIRICHLET0 = 1 };  /* face kinds */
 enum { MG_PREC_F64 = 0, MG_PREC_MIXED = 1 };        /* solver precision */
 enum { MG_SMOOTH_AUTO = 0, MG_SMOOTH_HALF = 1, MG_SMOOTH_FUSED = 2 };
 enum { MG_SMOOTH_DIRECT_READS = 4 };  /* flag for mg_smooth's color (see there) */
+enum { MG_PROLONG_CONSTANT = 0, MG_PROLONG_TRILINEAR = 1 };  /* prolongation forms */
 
 /* Boundary conditions: kind[d][0] / kind[d][1] for the low / high face of dimension d.
  * A periodic dimension must be periodic on both faces.  MG_BC_DIRICHLET0 is homogeneous
@@ -90,6 +91,12 @@ typedef struct {
                          boxes (or the periodic image, or the negated boundary cell across a
                          Dirichlet face) directly instead of first filling one ghost layer:
                          the same values, without the fill launches.  0: always fill. */
+  int prolong;        /* MG_PROLONG_CONSTANT (default): piecewise-constant injection;
+                         MG_PROLONG_TRILINEAR: per dimension 3/4 parent + 1/4 neighbour
+                         towards the fine cell (x, then y, then z), from the coarse level's
+                         filled first ghost layer.  Trilinear runs every level as separate
+                         launches (coarse_cells is ignored).  With the 8-cell-average
+                         restriction it does not converge faster than injection. */
 } mg_options;
 
 typedef struct {
@@ -263,6 +270,12 @@ int mg_restrict(mg_ctx_t ctx, mg_fab_t fine, mg_fab_t coarse, void* stream);
 
 /* Piecewise-constant prolongation added to the fine field: fine(c) += coarse(floor(c/2)). */
 int mg_prolong_add(mg_ctx_t ctx, mg_fab_t coarse, mg_fab_t fine, void* stream);
+
+/* Trilinear prolongation added to the fine field (the MG_PROLONG_TRILINEAR form of
+ * mg_options): per dimension 3/4 of the parent plus 1/4 of the parent's neighbour on the fine
+ * cell's side, dimension by dimension (x, y, z), each step fma(1/4, b, 3/4 * a).  coarse needs
+ * one ghost layer, filled beforehand (mg_fill_boundary); MG_EINVAL without ghosts. */
+int mg_prolong_add_trilinear(mg_ctx_t ctx, mg_fab_t coarse, mg_fab_t fine, void* stream);
 
 /* Exact bottom solve on a box array of at most 1024 cells: phi = M rhs with M from
  * mg_bottom_matrix (FP64 arithmetic for either fab type). */

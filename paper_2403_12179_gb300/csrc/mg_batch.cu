@@ -129,7 +129,9 @@ struct CoarseB {
 
 struct LevelLists {
   SegB half, half_all, rr, prolong;
+  SegB prolong3;  // trilinear prolongation (members solving with that form)
   TagB fill1_half, fill1_all, fill2_phi, fill2_phi2, fill_rhs;
+  TagB fill_c;    // the coarse level's phi, one layer, before the trilinear prolongation
   UnitB fab, fba;
   JobB bottom_next;      // bottoms at level l + 1
   CoarseB coarse_next;   // coarse cycles from level l + 1
@@ -214,7 +216,13 @@ void build_lists(Ctx& c, StepLists& S, const std::vector<Member*>& run,
       if (!D.direct) LL.fill1_all.add(fill_plan(c, *D.phi, &H.bc, 1), D.phi->base);
       LL.half_all.add(D.smooth, m->slot);
       LL.rr.add(D.rr, m->slot);
-      LL.prolong.add(D.prolong, m->slot);
+      if (H.p.prolong == MG_PROLONG_TRILINEAR) {
+        LL.prolong3.add(D.prolong, m->slot);
+        FabObj& cphi = *H.L[l + 1].phi;
+        LL.fill_c.add(fill_plan(c, cphi, &H.bc, 1), cphi.base);
+      } else {
+        LL.prolong.add(D.prolong, m->slot);
+      }
       if (l + 1 == H.lc) LL.coarse_next.add(H);
       else if (l + 2 == nl) LL.bottom_next.add(H);
     }
@@ -238,8 +246,9 @@ void upload_lists(Ctx& c, StepLists& S, Staging& st, cudaStream_t s) {
   auto job = [&](JobB& b) { b.off = st.push(b.v); };
   auto cjob = [&](CoarseB& b) { b.off = st.push(b.v); };
   for (LevelLists& LL : S.L) {
-    seg(LL.half); seg(LL.half_all); seg(LL.rr); seg(LL.prolong);
+    seg(LL.half); seg(LL.half_all); seg(LL.rr); seg(LL.prolong); seg(LL.prolong3);
     tag(LL.fill1_half); tag(LL.fill1_all); tag(LL.fill2_phi); tag(LL.fill2_phi2); tag(LL.fill_rhs);
+    tag(LL.fill_c);
     unit(LL.fab); unit(LL.fba);
     job(LL.bottom_next);
     cjob(LL.coarse_next);
@@ -320,8 +329,12 @@ void enqueue_step(Ctx& c, StepLists& S, const unsigned char* dev, unsigned long 
   }
   for (int l = nlev - 1; l >= 0; --l) {
     LevelLists& LL = S.L[l];
-    if (!LL.prolong.total) continue;
-    MG_CK(launch_prolong_add_l(S.dt, mk(LL.prolong, dev), LL.prolong.total, s));
+    if (!LL.prolong.total && !LL.prolong3.total) continue;
+    if (LL.prolong.total) MG_CK(launch_prolong_add_l(S.dt, mk(LL.prolong, dev), LL.prolong.total, s));
+    if (LL.prolong3.total) {
+      fill_l(c, S.dt, LL.fill_c, dev, s);
+      MG_CK(launch_prolong_trilinear_l(S.dt, mk(LL.prolong3, dev), LL.prolong3.total, s));
+    }
     smooth_l(c, S, LL, S.nu2, dev, err, s);
   }
   if (S.mixed && S.correct0.total)

@@ -518,6 +518,38 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(SegList L, long long n
   });
 }
 
+// Trilinear form: fine(c) += e(c), e interpolated between the parent P (weight 3/4) and P's
+// neighbour on c's side (1/4) in each dimension -- x, then y, then z, each step
+// fma(1/4, b, 3/4 * a) -- from the coarse field's first ghost layer where P is a boundary
+// cell of its box (filled beforehand).  G lanes per fine x-line.
+template <class T>
+__device__ __forceinline__ T lerp34(T a, T b) {
+  return Ar<T>::fma(T(0.25), b, Ar<T>::mul(T(0.75), a));
+}
+template <class T, int G>
+__global__ void __launch_bounds__(kThreads) k_prolong_trilinear(SegList L, long long nrows, long long per) {
+  const int lane = threadIdx.x & (G - 1);
+  for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int) {
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)lr % n1, z = (int)lr / n1;
+    const int ox = R.lo[0] & 1, oy = R.lo[1] & 1, oz = R.lo[2] & 1;
+    T* f = line<T>(R.v[0], y, z);
+    const T* c = line<T>(R.c[0], (y + oy) >> 1, (z + oz) >> 1);
+    // the neighbouring coarse row / plane on this fine row's side of its parents
+    const long long dy = ((y + oy) & 1) ? R.c[0].pitch : -(long long)R.c[0].pitch;
+    const long long dz = ((z + oz) & 1) ? R.c[0].plane : -R.c[0].plane;
+    for (int x = lane; x < n0; x += G) {
+      const T* q = c + ((x + ox) >> 1);
+      const int dx = ((x + ox) & 1) ? 1 : -1;
+      const T ux00 = lerp34(q[0], q[dx]);
+      const T ux10 = lerp34(q[dy], q[dy + dx]);
+      const T ux01 = lerp34(q[dz], q[dz + dx]);
+      const T ux11 = lerp34(q[dy + dz], q[dy + dz + dx]);
+      f[x] = Ar<T>::add(f[x], lerp34(lerp34(ux00, ux10), lerp34(ux01, ux11)));
+    }
+  });
+}
+
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_set_valid(SegList L, long long nrows, long long per,
                                                         T value) {
@@ -848,6 +880,23 @@ cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows
   return cudaGetLastError();
 }
 
+cudaError_t launch_prolong_trilinear_l(int dt, const SegList& L, long long nrows, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  const int G = group_lanes(L.width, 1, 8, 32);
+  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  if (dt == DT_F64) {
+    if (G == 32) k_prolong_trilinear<double, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+    else if (G == 16) k_prolong_trilinear<double, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+    else k_prolong_trilinear<double, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+  } else {
+    if (G == 32) k_prolong_trilinear<float, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+    else if (G == 16) k_prolong_trilinear<float, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+    else k_prolong_trilinear<float, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   const int G = group_lanes(L.width, 1, 8, 32);
@@ -928,6 +977,11 @@ cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows,
 cudaError_t launch_prolong_add(int dt, const DRow* rows, int nbox, long long nrows,
                                cudaStream_t s, int width) {
   return launch_prolong_add_l(dt, one_seg(rows, nbox, 0, width), nrows, s);
+}
+
+cudaError_t launch_prolong_trilinear(int dt, const DRow* rows, int nbox, long long nrows,
+                                     cudaStream_t s, int width) {
+  return launch_prolong_trilinear_l(dt, one_seg(rows, nbox, 0, width), nrows, s);
 }
 
 cudaError_t launch_bottom(int dt, const BottomJob* jobs, int njobs, int maxN, cudaStream_t s) {

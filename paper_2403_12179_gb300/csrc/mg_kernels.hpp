@@ -200,6 +200,9 @@ cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows,
 // Rows are fine x-lines.  v[0] = fine field (+=); c[0] = coarse field.
 cudaError_t launch_prolong_add(int dt, const DRow* rows, int nbox, long long nrows,
                                cudaStream_t s, int width = 0);
+// The trilinear form (same rows); reads the coarse field's first ghost layer (filled).
+cudaError_t launch_prolong_trilinear(int dt, const DRow* rows, int nbox, long long nrows,
+                                     cudaStream_t s, int width = 0);
 
 // Fused red + black sweep (see mg_fused.cu).  Rows: v[0] = source phi (2 ghost layers,
 // filled), v[1] = rhs (1 ghost layer, filled), v[2] = destination phi with the source's
@@ -260,6 +263,7 @@ cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigne
 cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s,
                                        bool direct = false);
 cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cudaStream_t s);
+cudaError_t launch_prolong_trilinear_l(int dt, const SegList& L, long long nrows, cudaStream_t s);
 cudaError_t launch_set_valid_l(int dt, const SegList& L, long long nrows, double value, cudaStream_t s);
 cudaError_t launch_maxabs_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
                             cudaStream_t s);

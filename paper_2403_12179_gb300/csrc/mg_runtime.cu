@@ -559,6 +559,7 @@ SolveParams params_from(const mg_options* o, const BoxArray& ba) {
     p.h = o->h;
     p.coarse_cells = o->coarse_cells;
     p.direct_reads = o->direct_reads;
+    p.prolong = o->prolong;
   }
   if (p.h <= 0.0) p.h = 1.0 / ba.dom.len(0);
   if (p.nu1 < 0 || p.nu2 < 0 || p.max_iter < 0 || p.nu1 + p.nu2 == 0)
@@ -567,6 +568,8 @@ SolveParams params_from(const mg_options* o, const BoxArray& ba) {
     fail(MG_EINVAL, "unknown precision mode");
   if (p.smoother < MG_SMOOTH_AUTO || p.smoother > MG_SMOOTH_FUSED)
     fail(MG_EINVAL, "unknown smoother");
+  if (p.prolong != MG_PROLONG_CONSTANT && p.prolong != MG_PROLONG_TRILINEAR)
+    fail(MG_EINVAL, "unknown prolongation");
   return p;
 }
 
@@ -1263,6 +1266,28 @@ int mg_prolong_add(mg_ctx_t h, mg_fab_t coarse, mg_fab_t fine, void* stream) {
       }, c->stream);
     });
     MG_CK(launch_prolong_add(ff->dtype, t.rows(), t.nbox, t.nrows, s, t.width));
+    return MG_OK;
+  });
+}
+
+int mg_prolong_add_trilinear(mg_ctx_t h, mg_fab_t coarse, mg_fab_t fine, void* stream) {
+  return guard([&] {
+    Ctx* c = (Ctx*)h;
+    if (!c) fail(MG_EINVAL, "ctx is NULL");
+    auto ff = c->get_fab(fine);
+    auto fc = c->get_fab(coarse);
+    if (fc->dtype != ff->dtype) fail(MG_EINVAL, "coarse and fine types differ");
+    if (fc->lay.g < 1) fail(MG_EINVAL, "trilinear prolongation reads one coarse ghost layer");
+    std::vector<int> map = coarse_map(*ff, *fc);
+    cudaStream_t s = S(stream);
+    const BoxArray& F = ff->ba->ba;
+    const OpTable& t = op_table(*c, "prolong", {coarse, fine}, 1.0, [&] {
+      return make_table(*c, F, 0, 1.0, 0, [&](int b, DRow& R) {
+        R.v[0] = ff->view(b);
+        R.c[0] = coarse_view(*fc, map[b], F.boxes[b]);
+      }, c->stream);
+    });
+    MG_CK(launch_prolong_trilinear(ff->dtype, t.rows(), t.nbox, t.nrows, s, t.width));
     return MG_OK;
   });
 }

@@ -304,6 +304,7 @@ std::vector<DTag> device_tags(const BoxArray& ba, const FabLayout& lay,
 struct SolveParams {
   int nu1 = 2, nu2 = 2, max_iter = 50, precision = MG_PREC_F64, smoother = MG_SMOOTH_AUTO;
   int use_graph = 1, fixed_vcycles = -1, coarse_cells = 0, direct_reads = 1;
+  int prolong = MG_PROLONG_CONSTANT;
   double h = 0.0;
 };
 SolveParams params_from(const mg_options* o, const BoxArray& ba);

@@ -161,7 +161,9 @@ void build_tables(Ctx& c, Hierarchy& H, cudaStream_t s) {
   // `limit` cells whose levels (down to the bottom) fit into shared memory.
   H.lc = nl;
   const int limit = H.p.coarse_cells != 0 ? H.p.coarse_cells : (H.dt == DT_F64 ? 512 : 4096);
-  for (int l = std::max(0, nl - kMaxCoarseLevels); H.p.coarse_cells >= 0 && l + 1 < nl; ++l) {
+  // (the coarse-cycle kernel prolongs by injection: the trilinear form runs level by level)
+  const bool one_launch = H.p.coarse_cells >= 0 && H.p.prolong == MG_PROLONG_CONSTANT;
+  for (int l = std::max(0, nl - kMaxCoarseLevels); one_launch && l + 1 < nl; ++l) {
     if (H.L[l].bao->ba.dom.npts() > limit) continue;
     int ext[kMaxCoarseLevels][3];
     for (int k = l; k < nl; ++k)
@@ -240,7 +242,8 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
     if (h->rhs_id == rhs.id && h->phi_id == phi.id && h->bc_key == key &&
         h->p.nu1 == p.nu1 && h->p.nu2 == p.nu2 && h->p.precision == p.precision &&
         h->p.smoother == p.smoother && h->p.h == p.h &&
-        h->p.coarse_cells == p.coarse_cells && h->p.direct_reads == p.direct_reads)
+        h->p.coarse_cells == p.coarse_cells && h->p.direct_reads == p.direct_reads &&
+        h->p.prolong == p.prolong)
       return *h;
   }
   if (rhs.dtype != DT_F64 || phi.dtype != DT_F64) fail(MG_EINVAL, "mg_solve needs FP64 fabs");
@@ -346,8 +349,14 @@ void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s, unsigned long long* no
   else MG_CK(launch_bottom(H.dt, (const BottomJob*)H.job->p, 1, H.N, s));
   for (int l = top - 1; l >= 0; --l) {
     LevelData& D = H.L[l];
-    MG_CK(launch_prolong_add(H.dt, D.prolong.rows(), D.prolong.nbox, D.prolong.nrows, s,
-                             D.prolong.width));
+    if (H.p.prolong == MG_PROLONG_TRILINEAR) {
+      launch_fill(c, *H.L[l + 1].phi, &H.bc, s, 1);  // the coarse neighbours it reads
+      MG_CK(launch_prolong_trilinear(H.dt, D.prolong.rows(), D.prolong.nbox, D.prolong.nrows, s,
+                                     D.prolong.width));
+    } else {
+      MG_CK(launch_prolong_add(H.dt, D.prolong.rows(), D.prolong.nbox, D.prolong.nrows, s,
+                               D.prolong.width));
+    }
     smooth(c, H, D, H.p.nu2, s, l == 0 ? norm0 : nullptr);
   }
 }

@@ -25,6 +25,7 @@ MG_BC_PERIODIC, MG_BC_DIRICHLET0 = 0, 1
 MG_PREC_F64, MG_PREC_MIXED = 0, 1
 MG_SMOOTH_AUTO, MG_SMOOTH_HALF, MG_SMOOTH_FUSED = 0, 1, 2
 MG_SMOOTH_DIRECT_READS = 4
+MG_PROLONG_CONSTANT, MG_PROLONG_TRILINEAR = 0, 1
 
 _c_int3 = ctypes.c_int * 3
 
@@ -38,7 +39,7 @@ class mg_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("fixed_vcycles", ctypes.c_int),
                 ("h", ctypes.c_double), ("coarse_cells", ctypes.c_int),
-                ("direct_reads", ctypes.c_int)]
+                ("direct_reads", ctypes.c_int), ("prolong", ctypes.c_int)]
 
 
 class mg_result(ctypes.Structure):
@@ -105,9 +106,10 @@ def make_bc(periodic=(1, 1, 1)):
 
 
 def make_options(nu1=2, nu2=2, max_iter=50, precision=MG_PREC_F64, smoother=MG_SMOOTH_AUTO,
-                 use_graph=1, fixed_vcycles=-1, h=0.0, coarse_cells=0, direct_reads=1):
+                 use_graph=1, fixed_vcycles=-1, h=0.0, coarse_cells=0, direct_reads=1,
+                 prolong=MG_PROLONG_CONSTANT):
     return mg_options(nu1, nu2, max_iter, precision, smoother, use_graph, fixed_vcycles, h,
-                      coarse_cells, direct_reads)
+                      coarse_cells, direct_reads, prolong)
 
 
 # ---- context -------------------------------------------------------------------------
@@ -314,6 +316,11 @@ def mg_restrict(ctx, fine, coarse, stream=None):
 
 def mg_prolong_add(ctx, coarse, fine, stream=None):
     _ck(lib().mg_prolong_add(ctx, ctypes.c_int64(coarse), ctypes.c_int64(fine), _s(stream)))
+
+
+def mg_prolong_add_trilinear(ctx, coarse, fine, stream=None):
+    _ck(lib().mg_prolong_add_trilinear(ctx, ctypes.c_int64(coarse), ctypes.c_int64(fine),
+                                       _s(stream)))
 
 
 def mg_bottom_solve(ctx, rhs, phi, bc, h, stream=None):

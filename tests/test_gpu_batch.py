@@ -39,27 +39,31 @@ def _make(ctx, n, box, periodic, seed, ng=(2, 1)):
     return rhs, fr, fp
 
 
-def _alone(ctx, n, box, periodic, seed, precision, smoother=mg.MG_SMOOTH_AUTO):
+def _alone(ctx, n, box, periodic, seed, precision, smoother=mg.MG_SMOOTH_AUTO,
+           prolong=mg.MG_PROLONG_CONSTANT):
     rhs, fr, fp = _make(ctx, n, box, periodic, seed)
     res = mg.mg_solve(ctx, fr, fp, mg.make_bc(periodic), 1e-10,
-                      mg.make_options(precision=precision, smoother=smoother))
+                      mg.make_options(precision=precision, smoother=smoother, prolong=prolong))
     phi = gu.fab_dense(ctx, fp, rhs.shape)
     mg.mg_fab_free(ctx, fr)
     mg.mg_fab_free(ctx, fp)
     return phi, res
 
 
-@pytest.mark.parametrize("precision,smoother", [(mg.MG_PREC_F64, mg.MG_SMOOTH_AUTO),
-                                               (mg.MG_PREC_MIXED, mg.MG_SMOOTH_AUTO),
-                                               (mg.MG_PREC_F64, mg.MG_SMOOTH_FUSED),
-                                               (mg.MG_PREC_MIXED, mg.MG_SMOOTH_FUSED)])
-def test_batch_equals_alone_bitwise(gctx, precision, smoother):
-    alone = [_alone(gctx, n, b, p, 100 + i, precision, smoother)
+TRI = mg.MG_PROLONG_TRILINEAR
+
+
+@pytest.mark.parametrize("precision,smoother,prolong",
+                         [(mg.MG_PREC_F64, mg.MG_SMOOTH_AUTO, 0), (mg.MG_PREC_MIXED, mg.MG_SMOOTH_AUTO, 0),
+                          (mg.MG_PREC_F64, mg.MG_SMOOTH_FUSED, 0), (mg.MG_PREC_MIXED, mg.MG_SMOOTH_FUSED, 0),
+                          (mg.MG_PREC_F64, mg.MG_SMOOTH_AUTO, TRI), (mg.MG_PREC_MIXED, mg.MG_SMOOTH_FUSED, TRI)])
+def test_batch_equals_alone_bitwise(gctx, precision, smoother, prolong):
+    alone = [_alone(gctx, n, b, p, 100 + i, precision, smoother, prolong)
              for i, (n, b, p) in enumerate(PROBLEMS)]
     made = [_make(gctx, n, b, p, 100 + i) for i, (n, b, p) in enumerate(PROBLEMS)]
     res = mg.mg_solve_batch(gctx, [m[1] for m in made], [m[2] for m in made],
                             [mg.make_bc(p) for (_, _, p) in PROBLEMS], 1e-10,
-                            mg.make_options(precision=precision, smoother=smoother))
+                            mg.make_options(precision=precision, smoother=smoother, prolong=prolong))
     for (rhs, fr, fp), r, (phi_a, res_a) in zip(made, res, alone):
         assert r.status == mg.MG_OK and res_a.status == mg.MG_OK
         assert r.vcycles == res_a.vcycles and r.rel_resid <= 1e-10
@@ -117,8 +121,9 @@ def test_serving_results_equal_alone(precision):
 
 def test_serving_many_members_both_precisions_equal_alone():
     """More members than the initial norm slots hold (the arrays grow while members run),
-    FP64 and mixed-precision members (half-sweep and fused smoothers) at once, later requests
-    joining running ones: every result and V-cycle count equals the solve alone."""
+    FP64 and mixed-precision members (half-sweep and fused smoothers, injection and trilinear
+    prolongation) at once, later requests joining running ones: every result and V-cycle
+    count equals the solve alone."""
     ctx = mg.mg_init(0)
     actx = mg.mg_init(0)
     try:
@@ -126,12 +131,14 @@ def test_serving_many_members_both_precisions_equal_alone():
         specs = [PROBLEMS[i % len(PROBLEMS)] for i in range(count)]
         precs = [mg.MG_PREC_F64 if i % 3 == 0 else mg.MG_PREC_MIXED for i in range(count)]
         smooth = [mg.MG_SMOOTH_FUSED if i % 3 == 2 else mg.MG_SMOOTH_AUTO for i in range(count)]
+        prol = [mg.MG_PROLONG_TRILINEAR if i % 4 == 3 else mg.MG_PROLONG_CONSTANT for i in range(count)]
         made, tickets = [], []
         for i, ((n, b, p), pr) in enumerate(zip(specs, precs)):
             m = _make(ctx, n, b, p, 400 + i)
             made.append(m)
             tickets.append(mg.mg_submit(ctx, m[1], m[2], mg.make_bc(p), 1e-10,
-                                        mg.make_options(precision=pr, smoother=smooth[i])))
+                                        mg.make_options(precision=pr, smoother=smooth[i],
+                                                        prolong=prol[i])))
             if i % 12 == 11:
                 time.sleep(0.02)
         res = [mg.mg_poll(ctx, t, -1)[1] for t in tickets]
@@ -140,7 +147,7 @@ def test_serving_many_members_both_precisions_equal_alone():
         for i, ((n, b, p), pr, (rhs, fr, fp), r) in enumerate(zip(specs, precs, made, res)):
             assert r.status == mg.MG_OK and r.rel_resid <= 1e-10
             phi = gu.fab_dense(ctx, fp, rhs.shape)
-            phi_a, res_a = _alone(actx, n, b, p, 400 + i, pr, smooth[i])
+            phi_a, res_a = _alone(actx, n, b, p, 400 + i, pr, smooth[i], prol[i])
             assert res_a.vcycles == r.vcycles, (i, n, b, p, pr)
             assert np.array_equal(phi, phi_a)
     finally:

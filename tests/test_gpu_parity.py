@@ -171,6 +171,61 @@ def test_restrict_and_prolong_bitwise(gctx, orc):
         assert np.array_equal(gu.valid(a, 1), gu.valid(p, 1))
 
 
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (1, 0, 1)])
+def test_trilinear_prolong_bitwise(gctx, orc, periodic):
+    """The trilinear prolongation entry point, on coarse ghosts filled by mg_fill_boundary,
+    equals the oracle's (fill, then trilinear prolongation) bit for bit."""
+    dom, mb = (31, 15, 23), (8, 8, 8)
+    ba, boxes = _ba(gctx, dom, mb)
+    levels = orc.hierarchy(Z3, dom, boxes)
+    cba = mg.mg_hierarchy_level(gctx, ba, 1)
+    cboxes = mg.mg_box_array_info(gctx, cba)[1]
+    g = inputs.rng(37)
+    fine = [g.standard_normal(f.shape) for f in orc.new_field(boxes, 1)]
+    coarse = [g.standard_normal(f.shape) for f in orc.new_field(cboxes, 1)]
+    ff, fc = gu.to_fab(gctx, ba, fine, 1), gu.to_fab(gctx, cba, coarse, 1)
+    mg.mg_fill_boundary(gctx, fc, mg.make_bc(periodic))
+    mg.mg_prolong_add_trilinear(gctx, fc, ff)
+    cref = orc.fill_boundary(levels[1][0], levels[1][1], periodic, cboxes, coarse, 1)
+    p_ref = orc.prolong_add(levels[1], cref, 1, levels[0], fine, 1, trilinear=True)
+    for a, p in zip(gu.from_fab(gctx, ff, len(boxes)), p_ref):
+        assert np.array_equal(gu.valid(a, 1), gu.valid(p, 1))
+    with pytest.raises(mg.MgError):   # no coarse ghosts to read
+        mg.mg_prolong_add_trilinear(gctx, gu.to_fab(gctx, cba, [c[:, 1:-1, 1:-1, 1:-1] for c in coarse], 0), ff)
+
+
+@pytest.mark.parametrize("periodic,mb", [((1, 1, 1), (16, 16, 16)), ((0, 0, 0), (16, 8, 32)),
+                                         ((0, 1, 0), (8, 16, 16))])
+def test_trilinear_solve_matches_oracle(gctx, orc, periodic, mb):
+    """Solves with the trilinear prolongation: FP64 iterates and the converged result equal
+    the oracle's to the bottom-matrix rounding (1e-12), with the same V-cycle count; the mixed
+    form reaches the tolerance within the a-priori bound of the oracle's mixed result."""
+    n = 32
+    rhs = inputs.rng(44).standard_normal((n, n, n))
+    if all(periodic):
+        rhs = inputs.remove_mean(rhs)
+    dom = (n - 1,) * 3
+    oboxes = orc.chop(Z3, dom, mb)
+    tri = mg.MG_PROLONG_TRILINEAR
+    for k in (1, 2):
+        phi, res = _solve_pair(gctx, orc, n, mb, periodic, rhs, fixed=k, prolong=tri)
+        o_phi, _, vc, _ = orc.solve(Z3, dom, periodic, oboxes, 1.0 / n, rhs, fixed_vcycles=k,
+                                    trilinear=True)
+        assert res.vcycles == k == vc
+        assert np.abs(phi - o_phi).max() <= 1e-12 * np.abs(o_phi).max()
+    phi, res = _solve_pair(gctx, orc, n, mb, periodic, rhs, prolong=tri)
+    o_phi, st, vc, _ = orc.solve(Z3, dom, periodic, oboxes, 1.0 / n, rhs, trilinear=True)
+    assert res.status == mg.MG_OK and st == 0 and res.vcycles == vc and res.rel_resid <= 1e-10
+    assert np.abs(phi - o_phi).max() <= 1e-12 * np.abs(o_phi).max()
+    pmx, rmx = _solve_pair(gctx, orc, n, mb, periodic, rhs, prolong=tri, precision=mg.MG_PREC_MIXED)
+    o_mx, st, vc, _ = orc.solve(Z3, dom, periodic, oboxes, 1.0 / n, rhs, trilinear=True, mixed=True)
+    assert rmx.status == mg.MG_OK and rmx.rel_resid <= 1e-10 and abs(rmx.vcycles - vc) <= 1
+    d = pmx - o_mx
+    if all(periodic):
+        d -= d.mean()
+    assert np.abs(d).max() <= 2 * 0.06 * 1e-10 * np.abs(rhs).max() * (10 if all(periodic) else 1)
+
+
 @pytest.mark.parametrize("n,mb", [((2, 2, 2), (2, 2, 2)), ((3, 3, 3), (3, 3, 3)),
                                   ((4, 6, 2), (2, 3, 2)), ((8, 8, 8), (4, 8, 8))])
 @pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (0, 1, 0)])
@@ -209,13 +264,14 @@ def test_dense_roundtrip_and_set_val(gctx):
 # ---- whole solves ----------------------------------------------------------------------
 
 def _solve_pair(gctx, orc, n, mb, periodic, rhs, tol=1e-10, fixed=-1, precision=mg.MG_PREC_F64,
-                use_graph=1, ng=(1, 0)):
+                use_graph=1, ng=(1, 0), prolong=mg.MG_PROLONG_CONSTANT):
     dom = (n - 1,) * 3
     h = 1.0 / n
     ba, boxes = _ba(gctx, dom, mb)
     fr = gu.dense_fab(gctx, ba, rhs, ng[1])
     fp = mg.mg_fab_alloc(gctx, ba, 1, ng[0])
-    opt = mg.make_options(fixed_vcycles=fixed, precision=precision, use_graph=use_graph)
+    opt = mg.make_options(fixed_vcycles=fixed, precision=precision, use_graph=use_graph,
+                          prolong=prolong)
     res = mg.mg_solve(gctx, fr, fp, mg.make_bc(periodic), tol, opt)
     phi = gu.fab_dense(gctx, fp, rhs.shape)
     mg.mg_fab_free(gctx, fr)
