@@ -237,16 +237,8 @@ size_t coarse_smem_bytes(int dt, const int (*n)[3], int nlev) {
 }
 
 cudaError_t coarse_opt_in(int dt, size_t smem) {
-  static std::mutex mu;
-  static size_t opted[2] = {0, 0};
-  std::lock_guard<std::mutex> lk(mu);
-  const int k = dt == DT_F64 ? 0 : 1;
-  if (smem <= opted[k]) return cudaSuccess;
-  cudaError_t e = dt == DT_F64
-      ? cudaFuncSetAttribute(k_coarse_cycle<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-      : cudaFuncSetAttribute(k_coarse_cycle<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) opted[k] = smem;
-  return e;
+  return dt == DT_F64 ? opt_in_smem((const void*)k_coarse_cycle<double>, smem)
+                      : opt_in_smem((const void*)k_coarse_cycle<float>, smem);
 }
 
 cudaError_t launch_coarse_cycle(int dt, const CoarseJob* jobs, int njobs, size_t smem,

@@ -440,13 +440,8 @@ static cudaError_t launch_fused_t(const UnitList& L, long long nunits, int ty, i
   re = (re + align - 1) / align * align;
   size_t smem = ((size_t)NP * pe + (size_t)NR * re) * sizeof(T) + (NP + NR + kStageBars) * 8;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  static size_t opted_in = 0;  // largest dynamic shared memory size already allowed
-  if (smem > opted_in) {
-    cudaError_t e = cudaFuncSetAttribute(k_rbgs_fused<T, D, RS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    opted_in = smem;
-  }
+  cudaError_t e = opt_in_smem((const void*)k_rbgs_fused<T, D, RS>, smem);
+  if (e != cudaSuccess) return e;
   k_rbgs_fused<T, D, RS><<<(unsigned)nunits, kFusedThreads, smem, s>>>(L, ty, pe, re, err);
   count_launches(1);
   return cudaGetLastError();

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <cstdio>
 
 #include "mg_bits.hpp"
@@ -735,6 +737,20 @@ Grid row_grid(long long nrows, int blocks_per_sm, int rows_per_pass = kWarps) {
 static std::atomic<long long> g_launches{0};
 void count_launches(long long n) { g_launches += n; }
 long long launches_so_far() { return g_launches.load(); }
+
+cudaError_t opt_in_smem(const void* kernel, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> opted;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& o = opted[{kernel, dev}];
+  if (smem <= o) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) o = smem;
+  return e;
+}
 
 int num_sms() {
   static int n = 0;

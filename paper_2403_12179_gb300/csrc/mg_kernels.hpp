@@ -163,6 +163,10 @@ struct UnitList {
 
 int num_sms();
 
+// Raise a kernel's dynamic shared memory limit to at least smem on the current device (once
+// per kernel, device and size; thread-safe).
+cudaError_t opt_in_smem(const void* kernel, size_t smem);
+
 // Process-wide count of kernels enqueued by the launchers below (plus graph kernel nodes
 // per replay, added by the graph owner).
 void count_launches(long long n);
