@@ -754,7 +754,26 @@ def oracle_sample(wl_name, vcycles=None):
 def cpu_baseline(wl_name, vcycles, budget_s=10.0):
     """The oracle as it stands on the host cores, on about budget_s seconds of work: whole
     solves (the GPU's V-cycle count, fixed) repeated while they fit, else runs with one
-    V-cycle repeated and extrapolated to the solve."""
+    V-cycle repeated and extrapolated to the solve.  Beside it, the same oracle on one thread
+    (one setup run and one one-V-cycle run, extrapolated the same way)."""
+    out = _cpu_baseline_all_cores(wl_name, vcycles, budget_s)
+    if 1.0 / out["value"] > 2.0:  # one thread would take too long for a default run
+        return out
+    import oracle
+    oracle.set_threads(1)
+    try:
+        t0, t1, tv = oracle_sample(wl_name)
+    finally:
+        oracle.set_threads(int(os.environ["OMP_NUM_THREADS"]))
+    est = t0 + vcycles * tv
+    out["single_thread"] = {"value": round(1.0 / est, 6), "unit": "solves/s", "cores": 1,
+                            "sample": f"{wl_name}: one run with 0 V-cycles ({t0:.2f} s) and one "
+                                      f"with 1 ({t1:.2f} s) on one thread, extrapolated to "
+                                      f"{vcycles} V-cycles ({est:.2f} s)"}
+    return out
+
+
+def _cpu_baseline_all_cores(wl_name, vcycles, budget_s):
     import oracle
     wl = WORKLOADS[wl_name]
     n, box = wl["n"], wl["box"]

@@ -249,6 +249,11 @@ def prolong_add(coarse_level, coarse, ng_c, fine_level, fine, ng_f, trilinear=Fa
     return unpack(ff, fine)
 
 
+def set_threads(n):
+    """Threads of the oracle's parallel loops from now on; returns the count in effect."""
+    return int(_load().orc_set_threads(ctypes.c_int(int(n))))
+
+
 def bottom_matrix(n, periodic, h):
     """Closed-form inverse (Dirichlet) or pseudo-inverse (all periodic) of the bottom
     operator, ordered x fastest."""

@@ -43,6 +43,9 @@
 #include <cstdio>
 #include <vector>
 #include <algorithm>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -739,6 +742,17 @@ int orc_prolong(const int cdlo[3], const int cdhi[3], int cnbox, const int* cloh
     prolong_add(make_field(C, ng_c, 1, const_cast<double*>(coarse)), make_field(F, ng_f, 1, fine));
   }
   return ORC_OK;
+}
+
+// Threads of the oracle's OpenMP loops from now on (n >= 1); returns the count in effect.
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 int orc_bottom_matrix(const int n[3], const int periodic[3], double h, double* M) {
