@@ -504,12 +504,13 @@ def run_batched(args):
         assert all(r.status == 0 and r.rel_resid <= 1e-10 for r in res), "batched solve failed"
         return dt, res
 
-    out = {}
+    out, vcs = {}, {}
     for name, prec in (("mixed", mg.MG_PREC_MIXED), ("f64", mg.MG_PREC_F64)):
         for _ in range(max(1, args.warmup)):
             batch(prec)
-        ts = [batch(prec)[0] for _ in range(args.steps)]
-        out[name] = statistics.median(ts)
+        runs = [batch(prec) for _ in range(args.steps)]
+        out[name] = statistics.median(r[0] for r in runs)
+        vcs[name] = [r.vcycles for r in runs[-1][1]]
     phis64 = [_fab_to_dense(ctx, f, sh, stream) for f, sh in zip(fp, shapes)]
     batch(mg.MG_PREC_MIXED)
     diff = 0.0
@@ -541,10 +542,36 @@ def run_batched(args):
                        "edges": "32/48/64/96/128 (seed 4)", "box": 32},
             "f64_batched_solves_per_s": round(n / out["f64"], 2),
             "f64_one_at_a_time_solves_per_s": round(n / t_seq, 2),
-            "cell_updates_per_s_mixed": round(cells * 8 * 9 / out["mixed"], 1),
+            "cell_updates_per_s_mixed": round(sum(pb.n ** 3 * 4 * v for pb, v in
+                                                  zip(probs, vcs["mixed"])) / out["mixed"], 1),
+            "cell_updates": "finest level: 4 per cell per V-cycle (V(2,2)), each problem's own count",
             "max_abs_diff_mixed_vs_f64_mod_const": diff}
     mg.mg_finalize(ctx)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batched(probs)
     print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_batched(probs, budget_s=10.0):
+    """The oracle's mixed-precision solve on the batch's problems in order, whole solves, for
+    about budget_s seconds (a leading subset of the batch)."""
+    import oracle
+    oracle.build()
+    count, t = 0, time.perf_counter()
+    for pb in probs:
+        dom = (pb.n - 1,) * 3
+        boxes = oracle.chop((0, 0, 0), dom, (pb.box,) * 3)
+        _, st, _, _ = oracle.solve((0, 0, 0), dom, (1, 1, 1), boxes, 1.0 / pb.n, pb.rhs(), mixed=True)
+        if st != 0:
+            raise RuntimeError("oracle solve failed")
+        count += 1
+        if time.perf_counter() - t >= budget_s:
+            break
+    el = time.perf_counter() - t
+    return {"value": round(count / el, 6), "unit": "solves/s",
+            "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+            "sample": f"the first {count} of the {len(probs)} problems, whole oracle mixed solves, "
+                      f"in {el:.1f} s"}
 
 
 def run_serving(args):
