@@ -12,6 +12,8 @@ forms, brute force or exact identities:
 * restriction / prolongation identities and adjointness (P6)
 * Gauss-Seidel property (coloured residuals vanish), decomposition invariance (P5)
 * mixed-precision result within the a-priori error bound (P7)
+* the V-cycle schedule (sweep counts, colour order, transfers, bottom) and the mixed form's
+  outer iteration vs a dense composition of per-level matrices, one and two cycles
 """
 import numpy as np
 import pytest
@@ -400,3 +402,106 @@ def test_mixed_precision_within_error_bound(orc):
     assert np.abs(p64 - p32).max() <= 2 * 0.06 * tol * np.abs(rhs).max()
     assert v2 <= v1 + 2
     del A
+
+
+# ---- the V-cycle schedule against a dense composition of per-level operators ------------
+#
+# tests/dense_ref.DenseVCycle states the cycle (sweep counts, colour order, fresh neighbour
+# values before every colour, residual restriction, zero coarse guess, exact bottom,
+# injection) as products of dense matrices, independently of the oracle's box loops.  One
+# and two oracle cycles from a random phi_0 must equal it to rounding: a swapped colour
+# order, a wrong sweep count, a missing fill between colours on a multi-box level, a
+# transfer operator off by a factor, or a skipped coarse correction all move the iterate
+# by O(1) (the mutation test below checks that the pin sees such slips).
+
+VC_CASES = [((8, 8, 8), (4, 4, 4)), ((8, 4, 6), (4, 4, 3))]
+VC_FACES = [(0, 0, 0), (1, 1, 1), (1, 0, 1)]
+VC_NU = [(2, 2), (1, 1), (0, 2)]
+
+
+def _vc_problem(n, periodic, seed=21):
+    g = inputs.rng(seed)
+    shape = (n[2], n[1], n[0])
+    rhs = g.standard_normal(shape)
+    if all(periodic):
+        rhs = inputs.remove_mean(rhs)
+    return rhs, g.standard_normal(shape)
+
+
+@pytest.mark.parametrize("n,mb", VC_CASES)
+@pytest.mark.parametrize("periodic", VC_FACES)
+@pytest.mark.parametrize("nu", VC_NU)
+def test_vcycle_schedule_matches_dense_composition(orc, n, mb, periodic, nu):
+    h = 1.0 / n[0]
+    dlo, dhi = _dom(n)
+    boxes = orc.chop(dlo, dhi, mb)
+    rhs, phi0 = _vc_problem(n, periodic)
+    ref = dense_ref.DenseVCycle(n, periodic, h, *nu)
+    for k in (1, 2):
+        phi, st, vc, _ = orc.solve(dlo, dhi, periodic, boxes, h, rhs, phi0=phi0,
+                                   fixed_vcycles=k, nu1=nu[0], nu2=nu[1])
+        d = ref.run(phi0, rhs, k)
+        assert st == 0 and vc == k
+        assert np.abs(phi - d).max() <= 1e-13 * np.abs(d).max()
+
+
+@pytest.mark.parametrize("n,mb", VC_CASES)
+@pytest.mark.parametrize("periodic", VC_FACES)
+def test_mixed_outer_iteration_matches_dense_composition(orc, n, mb, periodic):
+    """The mixed form's outer iteration phi <- phi + V(rhs - A phi) (the inner cycle on the
+    residual scaled by an exact power of two, then scaled back) equals the FP64 dense cycle
+    applied to the residual, up to the inner cycle's binary32 rounding: each inner value
+    carries a few units of 2^-24 relative to the correction, so the bound is 2^-20 of the
+    largest correction."""
+    h = 1.0 / n[0]
+    dlo, dhi = _dom(n)
+    boxes = orc.chop(dlo, dhi, mb)
+    rhs, phi0 = _vc_problem(n, periodic)
+    ref = dense_ref.DenseVCycle(n, periodic, h)
+    for k in (1, 2):
+        phi, st, vc, _ = orc.solve(dlo, dhi, periodic, boxes, h, rhs, phi0=phi0, fixed_vcycles=k,
+                                   mixed=True)
+        d = ref.run(phi0, rhs, k)
+        assert st == 0 and vc == k
+        assert np.abs(phi - d).max() <= 2.0 ** -20 * np.abs(d - phi0).max()
+
+
+class _Mutant(dense_ref.DenseVCycle):
+    """DenseVCycle with one planted schedule slip."""
+
+    def __init__(self, slip, *a, **kw):
+        super().__init__(*a, **kw)
+        self.slip = slip
+
+    def sweeps(self, l, phi, rhs, count):
+        if self.slip == "black_first":
+            for _ in range(count):
+                phi = self.half_sweep(l, phi, rhs, 1)
+                phi = self.half_sweep(l, phi, rhs, 0)
+            return phi
+        if self.slip == "one_sweep_less" and count > 0:
+            count -= 1
+        return super().sweeps(l, phi, rhs, count)
+
+    def cycle(self, l, phi, rhs):
+        if self.slip == "sum_restriction" and l < len(self.ext) - 1:
+            phi = self.sweeps(l, phi, rhs, self.nu1)
+            rc = 8.0 * (self.R[l] @ (rhs - self.A[l] @ phi))
+            ec = self.cycle(l + 1, np.zeros_like(rc), rc)
+            return self.sweeps(l, phi + 8.0 * (self.R[l].T @ ec), rhs, self.nu2)
+        if self.slip == "no_coarse_correction" and l < len(self.ext) - 1:
+            return self.sweeps(l, self.sweeps(l, phi, rhs, self.nu1), rhs, self.nu2)
+        return super().cycle(l, phi, rhs)
+
+
+@pytest.mark.parametrize("slip", ["black_first", "one_sweep_less", "sum_restriction",
+                                  "no_coarse_correction"])
+def test_vcycle_pin_detects_schedule_slips(orc, slip):
+    n, mb, periodic = (8, 8, 8), (4, 4, 4), (0, 0, 0)
+    h = 1.0 / n[0]
+    dlo, dhi = _dom(n)
+    rhs, phi0 = _vc_problem(n, periodic)
+    phi, _, _, _ = orc.solve(dlo, dhi, periodic, orc.chop(dlo, dhi, mb), h, rhs, phi0=phi0,
+                             fixed_vcycles=1)
+    bad = _Mutant(slip, n, periodic, h).run(phi0, rhs, 1)
+    assert np.abs(phi - bad).max() > 1e-3 * np.abs(phi).max()
