@@ -296,18 +296,27 @@ int mg_bottom_solve(mg_ctx_t ctx, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, d
  * (278,784 bytes), held by every GPU that loads the library until the process exits; no
  * cudaMalloc, cudaFree or pool allocation happens in this call.  At most 1024 boxes
  * (MG_EINVAL beyond).  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture.  Every call shares the array and it keeps the last call's contents (the
- * accumulator is cleared at the start of each call), so calls that overlap on the GPU --
- * on different streams, or from different host threads -- race. */
+ * (cudaGetSymbolAddress) with that device current and caches it for the life of the
+ * process (after cudaDeviceReset the library must be loaded again); make that first call
+ * before any stream capture.  `stream` must belong to the current device (MG_EINVAL
+ * otherwise).  Every call shares the array and it keeps the last call's contents (the
+ * accumulator is cleared at the start of each call).  Calls from one process are
+ * serialised: each holds a process-wide lock until it has synchronised `stream`, so they do
+ * not overlap on the GPU; work that reached the array any other way while a call runs
+ * would race with it. */
 int mg_residual_norm_noalloc(const int dom_lo[3], const int dom_hi[3], int nbox, const int* lo_hi,
                              const double* phi, int phi_nghost, const double* rhs, int rhs_nghost,
                              double h, double* norm, void* stream);
 
 /* ---- solves --------------------------------------------------------------------------- */
 
-/* Synchronous V(nu1,nu2) solve of lap(phi) = rhs (FP64 fabs, 1 component, same box array;
- * phi is the initial guess and the result).  Stops when ||rhs - A phi||_inf <=
+/* Synchronous V(nu1,nu2) solve of lap(phi) = rhs (Sec. 2: the framework's linear solvers
+ * for cell-centered data; the paper names them without their numerics, so the cycle is the
+ * reading stated at the top of this file and in mg_options: red-black Gauss-Seidel,
+ * residual restriction by 8-cell means, injection, exact bottom solve) on FP64 fabs with 1
+ * component and the same box array (phi is the initial guess and the result).  Each stage
+ * is one launch over all boxes of a level (Sec. 3.2); the cycle is replayed as a CUDA
+ * graph.  Stops when ||rhs - A phi||_inf <=
  * tol ||rhs||_inf (checked before each V-cycle), or after max_iter V-cycles
  * (MG_NOT_CONVERGED).  rhs == 0 gives phi = 0.  With fully periodic faces rhs must have
  * zero mean (to within tol).  The coarse levels are allocated on first use and cached per
@@ -316,7 +325,8 @@ int mg_solve(mg_ctx_t ctx, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, double t
              const mg_options* opt, mg_result* res);
 
 /* Synchronous solve of n independent problems whose boxes are packed into one box table
- * per V-cycle stage (one launch per stage for all problems).  Each problem converges and
+ * per V-cycle stage (one launch per stage for all problems: Sec. 3.2's fused launch over
+ * many boxes, extended across solves; each solve is mg_solve's cycle, Sec. 2).  Each problem converges and
  * retires on its own; res[i] receives its result.  Returns MG_OK if every solve did. */
 int mg_solve_batch(mg_ctx_t ctx, int n, const mg_fab_t* rhs, const mg_fab_t* phi,
                    const mg_bc* bcs, double tol, const mg_options* opt, mg_result* res);
@@ -335,6 +345,24 @@ int mg_solve_batch(mg_ctx_t ctx, int n, const mg_fab_t* rhs, const mg_fab_t* phi
 int mg_submit(mg_ctx_t ctx, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, double tol,
               const mg_options* opt, mg_ticket_t* out);
 
+/* Queue a solve whose data lives in host memory (no counterpart in the paper): the domain
+ * [dom_lo, dom_hi] chopped into boxes of edge <= max_box (as mg_box_array_create), rhs a
+ * dense FP64 array (nz, ny, nx), x fastest, and phi a dense FP64 array of the same shape that
+ * receives the answer (and holds the initial guess if phi_is_guess is 1; else the guess is
+ * 0).  At admission the scheduler allocates the request's fine-level fabs (rhs with one ghost
+ * layer, phi with two) from the context pool together with its coarse levels -- a request
+ * waits in the queue until the pool can hold all of it -- and copies rhs in; at completion
+ * it copies phi out and releases everything in stream order.  The result's latency
+ * (mg_result.seconds, submit -> done) therefore includes both copies.  Pinned host memory
+ * (cudaHostAlloc) lets the copies run at full speed; rhs and phi must stay valid and
+ * untouched until mg_poll reports completion.  With phi_is_guess = 0, phi may be the rhs
+ * array itself (rhs is copied in before phi is written).  Otherwise as mg_submit: FP64 or mixed
+ * precision per opt, results bit-identical to mg_solve on the same data.
+ * Errors: MG_EINVAL (bad domain, box size or options), MG_EAGAIN (queue full). */
+int mg_submit_host(mg_ctx_t ctx, const int dom_lo[3], const int dom_hi[3], const int max_box[3],
+                   const mg_bc* bc, const double* rhs, double* phi, int phi_is_guess, double tol,
+                   const mg_options* opt, mg_ticket_t* out);
+
 /* Serving statistics since the scheduler started (no counterpart in the paper). */
 typedef struct {
   int64_t submitted, admitted, completed, steps;
@@ -350,6 +378,22 @@ int mg_server_stats_get(mg_ctx_t ctx, mg_server_stats* out);
  * *res filled when done (the ticket is then released), MG_PENDING if not done in time,
  * MG_EINVAL for an unknown ticket. */
 int mg_poll(mg_ctx_t ctx, mg_ticket_t ticket, int timeout_ms, mg_result* res);
+
+/* ---- calibration (Sec. 3.1-3.2 STREAM triad; FP64 rate) ------------------------------ */
+
+/* STREAM triad a = b + s c (computed as one fma per cell) on the valid cells of three
+ * one-component fabs of one box array and type: the bandwidth example of Sec. 3.1, launched
+ * either as ONE kernel over all boxes (per_box = 0, the fused launch of Sec. 3.2) or as one
+ * launch per box (per_box = 1, Sec. 3.2's unfused form).  Asynchronous on `stream`.
+ * Algorithmic traffic: 3 element sizes per cell.  Errors: MG_EINVAL (shapes differ). */
+int mg_triad(mg_ctx_t ctx, mg_fab_t a, mg_fab_t b, mg_fab_t c, double s, int per_box,
+             void* stream);
+
+/* FP64 rate probe (no counterpart in the paper): enqueues on `stream` (current device) one
+ * kernel of independent FP64 fused multiply-add chains, iters steps each, and returns the
+ * FP64 lane operations it issues in *lane_ops; timing it gives the device's FP64 issue rate,
+ * the ceiling of the FP64 stencil kernels.  Errors: MG_EINVAL (iters < 1). */
+int mg_calib_fp64(void* stream, int iters, int64_t* lane_ops);
 
 /* ---- instrumentation (no counterpart in the paper) ---------------------------------- */
 

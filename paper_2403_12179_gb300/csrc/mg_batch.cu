@@ -47,6 +47,10 @@ struct Member {
   mg_result res{};
   int64_t ticket = 0;
   double t_submit = -1.0;  // served solves: submission time
+  // host-memory requests: the fabs and box array the scheduler made for this solve, and
+  // where its answer goes
+  int64_t own_ba = 0, own_rhs = 0, own_phi = 0;
+  double* phi_host = nullptr;
 };
 
 // Segment-list builders (host side); offsets into the step's packed upload.
@@ -480,6 +484,12 @@ struct Ctx::Server {
     double tol;
     SolveParams p;
     double t_submit;
+    // host-memory requests (mg_submit_host): rhs == phi == 0, the box array chopped at
+    // submission, the fabs allocated from the pool at admission
+    std::shared_ptr<BoxArrayObj> hba;
+    const double* rhs_host = nullptr;
+    double* phi_host = nullptr;
+    int phi_is_guess = 0;
   };
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -500,6 +510,17 @@ struct Ctx::Server {
 
 
 namespace {
+
+// Releases, in stream order, what the scheduler made for a host-memory request.
+void release_own(Ctx& c, Member& m, cudaStream_t s) {
+  if (m.own_phi) release_fab(c, m.own_phi, s);
+  if (m.own_rhs) release_fab(c, m.own_rhs, s);
+  if (m.own_ba) {
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.bas.erase(m.own_ba);
+  }
+  m.own_ba = m.own_rhs = m.own_phi = 0;
+}
 
 void server_loop(Ctx* c) {
   Ctx::Server& S = *c->server;
@@ -533,13 +554,25 @@ void server_loop(Ctx* c) {
       m->res.t_admit = c->now();
       m->res.t_start = r.t_submit;
       try {
-        auto fr = c->get_fab(r.rhs);
-        auto fp = c->get_fab(r.phi);
+        int64_t rid = r.rhs, pid = r.phi;
+        if (r.hba) {
+          // the request's fine level comes from the pool too: rhs (1 ghost layer) and phi
+          // (2, so that the fused smoother may run on it), filled from host memory
+          m->own_ba = c->add_ba(r.hba);
+          m->own_rhs = rid = add_pool_fab(*c, r.hba, m->own_ba, 1, 1, DT_F64, s);
+          m->own_phi = pid = add_pool_fab(*c, r.hba, m->own_ba, 1, 2, DT_F64, s);
+          m->phi_host = r.phi_host;
+          dense_upload(*c, *c->get_fab(rid), r.rhs_host, s);
+          if (r.phi_is_guess) dense_upload(*c, *c->get_fab(pid), r.phi_host, s);
+        }
+        auto fr = c->get_fab(rid);
+        auto fp = c->get_fab(pid);
         std::lock_guard<std::recursive_mutex> hl(c->hier_mu);
         Hierarchy& H = get_hierarchy(*c, *fr, *fp, &r.bc, r.p);
         for (auto& h : c->hier)
           if (h.get() == &H) m->H = h;
       } catch (const MgError& e) {
+        release_own(*c, *m, s);
         if (e.code == MG_ENOMEM && !active.empty()) {
           // no room: back to the head of the queue until a running solve retires
           std::lock_guard<std::mutex> lk(S.mu);
@@ -551,6 +584,7 @@ void server_loop(Ctx* c) {
         finish(*c, *m);
         std::lock_guard<std::mutex> lk(S.mu);
         S.done[m->ticket] = m->res;
+        S.stats.completed += 1;
         S.cv_done.notify_all();
         continue;
       }
@@ -597,8 +631,7 @@ void server_loop(Ctx* c) {
     }
     // retire
     auto t_ret0 = std::chrono::steady_clock::now();
-    int64_t ncomp = 0;
-    std::vector<std::unique_ptr<Member>> keep;
+    std::vector<std::unique_ptr<Member>> keep, leaving;
     for (auto& m : active) {
       if (!m->done) {
         keep.push_back(std::move(m));
@@ -616,15 +649,41 @@ void server_loop(Ctx* c) {
           if (!(h->rhs_id == rid && h->phi_id == pid)) rest.push_back(h);
         c->hier.swap(rest);
       }
-      std::lock_guard<std::mutex> lk(S.mu);
-      S.done[m->ticket] = m->res;
-      ++ncomp;
-      S.cv_done.notify_all();
+      leaving.push_back(std::move(m));
     }
     active.swap(keep);
+    // host-memory requests: the answer goes back to the caller's array before completion
+    bool any_host = false;
+    for (auto& m : leaving)
+      if (m->own_phi) {
+        try {
+          if (m->phi_host)
+            dense_download(*c, *c->get_fab(m->own_phi), m->phi_host, s);
+        } catch (const MgError& e) {
+          if (m->res.status == MG_OK) m->res.status = e.code;
+        }
+        any_host = true;
+      }
+    if (any_host) {
+      if (cudaStreamSynchronize(s) != cudaSuccess)
+        for (auto& m : leaving)
+          if (m->own_phi && m->res.status == MG_OK) m->res.status = MG_ECUDA;
+      for (auto& m : leaving)
+        if (m->own_phi) {
+          m->res.t_end = c->now();
+          m->res.seconds = m->res.t_end - m->res.t_start;
+          release_own(*c, *m, s);
+        }
+    }
+    for (auto& m : leaving) {
+      // counted with the publication, so a caller that has polled every ticket sees them all
+      std::lock_guard<std::mutex> lk(S.mu);
+      S.done[m->ticket] = m->res;
+      S.stats.completed += 1;
+      S.cv_done.notify_all();
+    }
     {
       std::lock_guard<std::mutex> lk(S.mu);
-      S.stats.completed += ncomp;
       S.stats.retire_seconds += secs_since(t_ret0);
     }
   }
@@ -651,6 +710,35 @@ int server_submit(Ctx& c, int64_t rhs, int64_t phi, const mg_bc* bc, double tol,
   std::lock_guard<std::mutex> lk(S.mu);
   if (S.queue.size() >= S.max_queue) fail(MG_EAGAIN, "serving queue full");
   Ctx::Server::Req r{S.next_ticket++, rhs, phi, *bc, tol, p, c.now()};
+  S.stats.submitted += 1;
+  S.known[r.ticket] = true;
+  S.queue.push_back(r);
+  *ticket = r.ticket;
+  S.cv_work.notify_one();
+  return MG_OK;
+}
+
+int server_submit_host(Ctx& c, std::shared_ptr<BoxArrayObj> ba, const double* rhs, double* phi,
+                       int phi_is_guess, const mg_bc* bc, double tol, const SolveParams& p,
+                       int64_t* ticket) {
+  c.require_device();
+  if (!(tol >= 0)) fail(MG_EINVAL, "tol must be >= 0");
+  if (!rhs || !phi) fail(MG_EINVAL, "NULL host array");
+  int per[3];
+  bc_code(bc, per);
+  ba->hierarchy();  // MG_EINVAL now rather than at admission
+  if (!c.server) {
+    c.server = std::make_shared<Ctx::Server>();
+    c.server->th = std::thread(server_loop, &c);
+  }
+  Ctx::Server& S = *c.server;
+  std::lock_guard<std::mutex> lk(S.mu);
+  if (S.queue.size() >= S.max_queue) fail(MG_EAGAIN, "serving queue full");
+  Ctx::Server::Req r{S.next_ticket++, 0, 0, *bc, tol, p, c.now()};
+  r.hba = std::move(ba);
+  r.rhs_host = rhs;
+  r.phi_host = phi;
+  r.phi_is_guess = phi_is_guess ? 1 : 0;
   S.stats.submitted += 1;
   S.known[r.ticket] = true;
   S.queue.push_back(r);

@@ -564,6 +564,40 @@ __global__ void __launch_bounds__(kThreads) k_set_valid(SegList L, long long nro
   });
 }
 
+// STREAM triad a = b + s c (one fma) on valid cells: the calibration kernel of Sec. 3.1-3.2,
+// run either as one launch over all boxes or as one launch per box.  G lanes per x-line.
+template <class T, int G>
+__global__ void __launch_bounds__(kThreads) k_triad(SegList L, long long nrows, long long per, T s) {
+  const int lane = threadIdx.x & (G - 1);
+  for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int) {
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)lr % n1, z = (int)lr / n1;
+    T* __restrict__ a = line<T>(R.v[0], y, z);
+    const T* __restrict__ b = line<T>(R.v[1], y, z);
+    const T* __restrict__ c = line<T>(R.v[2], y, z);
+    for (int x = lane; x < n0; x += G) a[x] = Ar<T>::fma(s, __ldg(c + x), __ldg(b + x));
+  });
+}
+
+// FP64 throughput probe: 8 independent chains of fused multiply-adds per thread (a -> a b + c
+// converges to c / (1 - b), so the values stay normal).  The result is stored only if it
+// equals an impossible value, which keeps the chains alive without a memory write.
+__device__ double g_probe_sink;
+constexpr int kProbeChains = 8;
+__global__ void __launch_bounds__(256) k_fp64_probe(int iters, double b, double c) {
+  double a[kProbeChains];
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) a[k] = 1e-3 * threadIdx.x + k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = __fma_rn(a[k], b, c);
+  }
+  double s = a[0];
+#pragma unroll
+  for (int k = 1; k < kProbeChains; ++k) s = __dadd_rn(s, a[k]);
+  if (s == -1.0) g_probe_sink = s;
+}
+
 template <class T>
 __global__ void k_set_flat(T* p, long long n, T value) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -919,6 +953,33 @@ cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cuda
   const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
   if (dt == DT_F64) prolong_add_g<double>(G, g, s, L, nrows);
   else prolong_add_g<float>(G, g, s, L, nrows);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_triad_l(int dt, const SegList& L, long long nrows, double sc, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  const int G = group_lanes(L.width, 1, 8, 32);
+  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  if (dt == DT_F64) {
+    if (G == 32) k_triad<double, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, sc);
+    else if (G == 16) k_triad<double, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, sc);
+    else k_triad<double, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, sc);
+  } else {
+    const float f = (float)sc;
+    if (G == 32) k_triad<float, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, f);
+    else if (G == 16) k_triad<float, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, f);
+    else k_triad<float, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, f);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_probe(int iters, long long* lane_ops, cudaStream_t s) {
+  if (iters < 1) return cudaErrorInvalidValue;
+  const int blocks = num_sms() * 8;
+  k_fp64_probe<<<blocks, 256, 0, s>>>(iters, 0.999999, 1e-7);
+  if (lane_ops) *lane_ops = (long long)blocks * 256 * kProbeChains * iters;
   count_launches(1);
   return cudaGetLastError();
 }

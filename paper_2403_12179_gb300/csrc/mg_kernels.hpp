@@ -269,6 +269,11 @@ cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows
 cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cudaStream_t s);
 cudaError_t launch_prolong_trilinear_l(int dt, const SegList& L, long long nrows, cudaStream_t s);
 cudaError_t launch_set_valid_l(int dt, const SegList& L, long long nrows, double value, cudaStream_t s);
+// v[0] = a, v[1] = b, v[2] = c: a = fma(s, c, b) on valid cells.
+cudaError_t launch_triad_l(int dt, const SegList& L, long long nrows, double s, cudaStream_t st);
+// FP64 throughput probe: blocks x 256 threads, each running 8 independent chains of `iters`
+// fused multiply-adds; *lane_ops = the FP64 lane operations issued.
+cudaError_t launch_fp64_probe(int iters, long long* lane_ops, cudaStream_t s);
 cudaError_t launch_maxabs_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
                             cudaStream_t s);
 cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,

@@ -11,7 +11,8 @@
 // The array's name in host code is only a host-side stand-in for the device symbol: passing
 // it to a kernel would fault (or silently use the wrong memory where the GPU can reach host
 // memory).  The device address is looked up once per device with cudaGetSymbolAddress and
-// cached.
+// cached for the life of the process (after a cudaDeviceReset the library must be loaded
+// again).
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -63,6 +64,15 @@ extern "C" int mg_residual_norm_noalloc(const int dom_lo[3], const int dom_hi[3]
     int dev = 0;
     check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) fail(MG_EINVAL, "device index out of range");
+    if (s && s != cudaStreamLegacy && s != cudaStreamPerThread) {
+      // the scratch address belongs to the current device: a stream of another device
+      // could not reach it
+      int sdev = -1;
+      check_cuda(cudaStreamGetDevice(s, &sdev), "cudaStreamGetDevice");
+      if (sdev != dev)
+        fail(MG_EINVAL, "mg_residual_norm_noalloc: the stream belongs to another device than "
+                        "the current one");
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     char* scratch = (char*)scratch_address(dev);
     // Box table built in host static storage: each fab is laid out as mg_fab_layout

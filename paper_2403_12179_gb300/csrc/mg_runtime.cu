@@ -343,6 +343,60 @@ void ensure_valid_rows(Ctx& c, FabObj& f) {
   MG_CK(cudaStreamSynchronize(c.stream));
 }
 
+int64_t add_pool_fab(Ctx& c, std::shared_ptr<BoxArrayObj> ba, int64_t ba_id, int ncomp, int g,
+                     int dt, cudaStream_t s) {
+  auto f = std::make_shared<FabObj>();
+  f->ba_id = ba_id;
+  f->ba = std::move(ba);
+  f->dtype = dt;
+  f->lay = make_layout(f->ba->ba, ncomp, g, f->esize());
+  f->bytes = (size_t)f->lay.total * f->esize();
+  f->own = c.alloc(f->bytes, s);
+  f->base = f->own->p;
+  MG_CK(cudaMemsetAsync(f->base, 0, f->bytes, s));
+  std::lock_guard<std::mutex> lk(c.mu);
+  f->id = c.next_id++;
+  c.fabs[f->id] = f;
+  return f->id;
+}
+
+void release_fab(Ctx& c, int64_t id, cudaStream_t s) {
+  std::shared_ptr<FabObj> f;
+  {
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.fabs.find(id);
+    if (it == c.fabs.end()) return;
+    f = it->second;
+    c.fabs.erase(it);
+  }
+  if (f->valid_rows) f->valid_rows->reset(s);
+  if (f->own) f->own->reset(s);
+}
+
+void dense_upload(Ctx& c, FabObj& f, const void* host, cudaStream_t s) {
+  ensure_valid_rows(c, f);
+  const Box& D = f.ba->ba.dom;
+  int n[3] = {D.len(0), D.len(1), D.len(2)};
+  const size_t bytes = (size_t)D.npts() * f.lay.ncomp * f.esize();
+  DevBufP stage = c.alloc(bytes, s);
+  MG_CK(cudaMemcpyAsync(stage->p, host, bytes, cudaMemcpyHostToDevice, s));
+  MG_CK(launch_dense_copy(f.dtype, (const DRow*)f.valid_rows->p, (int)f.ba->ba.boxes.size(),
+                          f.nrows, stage->p, D.lo, n, f.lay.ncomp, 0, s));
+  stage->reset(s);
+}
+
+void dense_download(Ctx& c, FabObj& f, void* host, cudaStream_t s) {
+  ensure_valid_rows(c, f);
+  const Box& D = f.ba->ba.dom;
+  int n[3] = {D.len(0), D.len(1), D.len(2)};
+  const size_t bytes = (size_t)D.npts() * f.lay.ncomp * f.esize();
+  DevBufP stage = c.alloc(bytes, s);
+  MG_CK(launch_dense_copy(f.dtype, (const DRow*)f.valid_rows->p, (int)f.ba->ba.boxes.size(),
+                          f.nrows, stage->p, D.lo, n, f.lay.ncomp, 1, s));
+  MG_CK(cudaMemcpyAsync(host, stage->p, bytes, cudaMemcpyDeviceToHost, s));
+  stage->reset(s);
+}
+
 const std::vector<double>& bottom_matrix_t(Ctx& c, const int n[3], const int periodic[3],
                                            double h) {
   std::lock_guard<std::mutex> lk(c.bottom_mu);

@@ -226,6 +226,16 @@ FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc, int layers = -1);
 void launch_fill(Ctx& c, FabObj& f, const mg_bc* bc, cudaStream_t s, int layers = -1);
 void ensure_valid_rows(Ctx& c, FabObj& f);
 
+// Fabs owned by the library on behalf of a request (host-memory serving): allocated from the
+// pool and zero-filled on stream s (no synchronisation), registered under a new handle;
+// released in stream order on s.  Dense (nz, ny, nx) host arrays move in and out through a
+// pool staging buffer on s (the host memory must stay valid until s has passed the copy).
+int64_t add_pool_fab(Ctx& c, std::shared_ptr<BoxArrayObj> ba, int64_t ba_id, int ncomp, int g,
+                     int dt, cudaStream_t s);
+void release_fab(Ctx& c, int64_t id, cudaStream_t s);
+void dense_upload(Ctx& c, FabObj& f, const void* host, cudaStream_t s);
+void dense_download(Ctx& c, FabObj& f, void* host, cudaStream_t s);
+
 // Appends one row per box of `ba` to a host table; views(b, row) fills the views of box b.
 // kind 0: rows are fine x-lines; kind 1: rows are coarse x-lines (n/2 of each dimension).
 template <class F>
@@ -319,6 +329,9 @@ void destroy_hierarchies(Ctx& c);
 // Serving
 int server_submit(Ctx& c, int64_t rhs, int64_t phi, const mg_bc* bc, double tol,
                   const SolveParams& p, int64_t* ticket);
+int server_submit_host(Ctx& c, std::shared_ptr<BoxArrayObj> ba, const double* rhs, double* phi,
+                       int phi_is_guess, const mg_bc* bc, double tol, const SolveParams& p,
+                       int64_t* ticket);
 int server_poll(Ctx& c, int64_t ticket, int timeout_ms, mg_result* res);
 void server_stop(Ctx& c);
 void server_stats(Ctx& c, mg_server_stats* out);

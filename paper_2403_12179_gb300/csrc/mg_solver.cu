@@ -573,6 +573,25 @@ int mg_submit(mg_ctx_t h, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, double to
   });
 }
 
+int mg_submit_host(mg_ctx_t h, const int dom_lo[3], const int dom_hi[3], const int max_box[3],
+                   const mg_bc* bc, const double* rhs, double* phi, int phi_is_guess, double tol,
+                   const mg_options* opt, mg_ticket_t* out) {
+  return guard([&] {
+    Ctx* c = (Ctx*)h;
+    if (!c || !dom_lo || !dom_hi || !max_box || !out) fail(MG_EINVAL, "NULL argument");
+    auto b = std::make_shared<BoxArrayObj>();
+    Box dom;
+    for (int d = 0; d < 3; ++d) {
+      dom.lo[d] = dom_lo[d];
+      dom.hi[d] = dom_hi[d];
+    }
+    std::string err;
+    if (!chop(dom, max_box, &b->ba, &err)) fail(MG_EINVAL, err);
+    SolveParams p = params_from(opt, b->ba);
+    return server_submit_host(*c, std::move(b), rhs, phi, phi_is_guess, bc, tol, p, out);
+  });
+}
+
 int mg_server_stats_get(mg_ctx_t h, mg_server_stats* out) {
   return guard([&] {
     Ctx* c = (Ctx*)h;

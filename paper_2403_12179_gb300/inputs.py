@@ -129,6 +129,15 @@ class Request:
         r = rng(self.seed).standard_normal(size=(self.n, self.n, self.n))
         return np.ascontiguousarray(remove_mean(r) if self.periodic else r)
 
+    def rhs_into(self, out: np.ndarray) -> np.ndarray:
+        """The same values as rhs(), drawn into a caller's C-contiguous (n, n, n) float64
+        array (e.g. pinned host memory), without a temporary of the request's size."""
+        assert out.shape == (self.n,) * 3 and out.dtype == np.float64 and out.flags.c_contiguous
+        rng(self.seed).standard_normal(out=out)
+        if self.periodic:
+            out -= np.sum(out, dtype=np.float64) / out.size
+        return out
+
 
 def serving_requests(count: int = 5000, rate: float = 200.0, seed: int = 6,
                      edges=(32, 64, 128, 256), probs=(0.4, 0.3, 0.2, 0.1)):

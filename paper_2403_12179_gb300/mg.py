@@ -375,6 +375,18 @@ def mg_submit(ctx, rhs, phi, bc, tol=1e-10, opt=None):
     return t.value
 
 
+def mg_submit_host(ctx, dom_lo, dom_hi, max_box, bc, rhs_ptr, phi_ptr, phi_is_guess=False,
+                   tol=1e-10, opt=None):
+    """Queue a solve whose rhs / phi are dense FP64 host arrays (addresses; pinned memory
+    recommended) that must stay alive until mg_poll reports completion."""
+    t = ctypes.c_int64()
+    _ck(lib().mg_submit_host(ctx, _c_int3(*dom_lo), _c_int3(*dom_hi), _c_int3(*max_box),
+                             ctypes.byref(bc), ctypes.c_void_p(rhs_ptr), ctypes.c_void_p(phi_ptr),
+                             ctypes.c_int(1 if phi_is_guess else 0), ctypes.c_double(tol),
+                             ctypes.byref(opt) if opt is not None else None, ctypes.byref(t)))
+    return t.value
+
+
 class mg_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
                 ("completed", ctypes.c_int64), ("steps", ctypes.c_int64),
@@ -426,6 +438,19 @@ class BoxView:
     def __cuda_array_interface__(self):
         return {"shape": self.shape, "typestr": self.typestr, "data": (self.ptr, False),
                 "strides": self.strides, "version": 3}
+
+
+def mg_triad(ctx, a, b, c, s, per_box=False, stream=None):
+    """a = b + s c on valid cells: one launch over all boxes, or one launch per box."""
+    _ck(lib().mg_triad(ctx, ctypes.c_int64(a), ctypes.c_int64(b), ctypes.c_int64(c),
+                       ctypes.c_double(s), ctypes.c_int(1 if per_box else 0), _s(stream)))
+
+
+def mg_calib_fp64(stream, iters):
+    """Enqueue the FP64 rate probe on `stream`; returns the FP64 lane operations it issues."""
+    n = ctypes.c_int64()
+    _ck(lib().mg_calib_fp64(_s(stream), ctypes.c_int(iters), ctypes.byref(n)))
+    return n.value
 
 
 def mg_sweep_timing(ctx, enable):

@@ -295,3 +295,112 @@ def test_full_size_batched_512(gctx):
     for a, b in zip(fr, fp):
         mg.mg_fab_free(gctx, a)
         mg.mg_fab_free(gctx, b)
+
+
+# ---- serving from host memory (mg_submit_host) ------------------------------------------
+
+def _pinned(a):
+    t = torch.from_numpy(np.ascontiguousarray(a, np.float64)).pin_memory()
+    return t
+
+
+def _serve_host(ctx, specs, precision, seed0):
+    """Submit every spec as a host-memory request (pinned rhs and phi); returns the rhs, the
+    pinned phi tensors and the results."""
+    rhs, phis, tickets = [], [], []
+    for i, (n, b, p) in enumerate(specs):
+        r = _pinned(_rhs(n, p, seed0 + i))
+        ph = torch.zeros((n, n, n), dtype=torch.float64).pin_memory()
+        rhs.append(r)
+        phis.append(ph)
+        tickets.append(mg.mg_submit_host(ctx, (0, 0, 0), (n - 1,) * 3, (b,) * 3, mg.make_bc(p),
+                                         r.data_ptr(), ph.data_ptr(), False, 1e-10,
+                                         mg.make_options(precision=precision)))
+    res = [mg.mg_poll(ctx, t, -1)[1] for t in tickets]
+    return rhs, phis, res
+
+
+@pytest.mark.parametrize("precision", [mg.MG_PREC_F64, mg.MG_PREC_MIXED])
+def test_serving_from_host_equals_alone(precision):
+    """Requests whose rhs and phi live in (pinned) host memory: the scheduler allocates their
+    fine levels from the pool, copies rhs in and phi out; each answer equals the solve alone,
+    bit for bit, and the pool returns to its starting level once all have completed."""
+    ctx = mg.mg_init(0)
+    actx = mg.mg_init(0)
+    try:
+        _, pool0 = mg.mg_pool_info(ctx)
+        specs = PROBLEMS * 2
+        rhs, phis, res = _serve_host(ctx, specs, precision, 600)
+        for i, ((n, b, p), r, ph) in enumerate(zip(specs, res, phis)):
+            assert r.status == mg.MG_OK and r.rel_resid <= 1e-10
+            assert r.t_end >= r.t_admit >= r.t_start and r.seconds > 0
+            phi_a, res_a = _alone(actx, n, b, p, 600 + i, precision)
+            assert res_a.vcycles == r.vcycles
+            assert np.array_equal(ph.numpy(), phi_a)
+        assert mg.mg_server_stats_get(ctx)["completed"] == len(specs)
+        torch.cuda.synchronize()
+        time.sleep(0.05)
+        assert mg.mg_pool_info(ctx)[1] <= pool0 + (1 << 20)   # fine levels released too
+    finally:
+        mg.mg_finalize(ctx)
+        mg.mg_finalize(actx)
+
+
+def test_serving_from_host_admission_by_pool_room():
+    """A pool with room for about two whole host-memory requests (fine level, copies and
+    coarse levels): later ones wait in the queue until running ones retire; a request larger
+    than the empty pool completes with MG_ENOMEM; every other answer equals the solve alone."""
+    n, box, per = 64, 32, (0, 0, 0)
+    probe = mg.mg_init(0)
+    try:
+        ba = mg.mg_box_array_create(probe, (0, 0, 0), (n - 1,) * 3, (box,) * 3)
+        fine = mg.mg_fab_layout(probe, ba, 1, 1, mg.MG_F64) + mg.mg_fab_layout(probe, ba, 1, 2, mg.MG_F64)
+        rhs, fr, fp = _make(probe, n, box, per, 299)
+        _, before = mg.mg_pool_info(probe)
+        mg.mg_solve(probe, fr, fp, mg.make_bc(per), 1e-10)
+        _, after = mg.mg_pool_info(probe)
+    finally:
+        mg.mg_finalize(probe)
+    one = fine + (after - before) + 2 * n ** 3 * 8
+    ctx = mg.mg_init(0)
+    _, base = mg.mg_pool_info(ctx)
+    mg.mg_finalize(ctx)
+    ctx = mg.mg_init(0, base + int(2.5 * one) + (1 << 20))
+    actx = mg.mg_init(0)
+    try:
+        specs = [(n, box, per)] * 8
+        rhs, phis, res = _serve_host(ctx, specs, mg.MG_PREC_F64, 700)
+        assert all(r.status == mg.MG_OK for r in res)
+        first_end = min(r.t_end for r in res)
+        assert sum(r.t_admit >= first_end for r in res) >= 4
+        for i, (r, ph) in enumerate(zip(res, phis)):
+            phi_a, res_a = _alone(actx, n, box, per, 700 + i, mg.MG_PREC_F64)
+            assert np.array_equal(ph.numpy(), phi_a) and res_a.vcycles == r.vcycles
+        big = 256
+        rb = _pinned(_rhs(big, per, 799))
+        pb = torch.zeros((big,) * 3, dtype=torch.float64).pin_memory()
+        t = mg.mg_submit_host(ctx, (0, 0, 0), (big - 1,) * 3, (64,) * 3, mg.make_bc(per),
+                              rb.data_ptr(), pb.data_ptr(), False, 1e-10)
+        rc, r = mg.mg_poll(ctx, t, -1)
+        assert rc == mg.MG_OK and r.status == mg.MG_ENOMEM
+    finally:
+        mg.mg_finalize(ctx)
+        mg.mg_finalize(actx)
+
+
+def test_serving_from_host_with_initial_guess():
+    """phi_is_guess = 1 starts from the caller's phi: a converged answer submitted as its own
+    guess needs no V-cycle and comes back unchanged."""
+    ctx = mg.mg_init(0)
+    try:
+        n, b, p = 32, 16, (0, 0, 0)
+        rhs, phis, res = _serve_host(ctx, [(n, b, p)], mg.MG_PREC_F64, 800)
+        assert res[0].status == mg.MG_OK and res[0].vcycles > 0
+        guess = phis[0].clone().pin_memory()
+        t = mg.mg_submit_host(ctx, (0, 0, 0), (n - 1,) * 3, (b,) * 3, mg.make_bc(p),
+                              rhs[0].data_ptr(), guess.data_ptr(), True, 1e-10)
+        rc, r = mg.mg_poll(ctx, t, -1)
+        assert rc == mg.MG_OK and r.status == mg.MG_OK and r.vcycles == 0
+        assert torch.equal(guess, phis[0])
+    finally:
+        mg.mg_finalize(ctx)

@@ -677,3 +677,64 @@ def test_fused_sweep_rhs_staging_forced(orc, tmp_path, monkeypatch, rhs_smem, ty
             assert np.array_equal(gu.valid(a, 2), gu.valid(r, 2))
     finally:
         mg.mg_finalize(ctx)
+
+
+# ---- the mixed-precision form against the oracle's mixed form, iterate by iterate -------
+#
+# After k outer iterations (FP64 residual, exact power-of-two scaling into FP32, one FP32
+# V-cycle, FP64 correction) the GPU iterate equals the oracle's bit for bit: every FP32 and
+# FP64 stencil kernel rounds as the oracle does, the scaling and the correction are exact
+# operations or single roundings on both sides, and the bottom solve sums in FP64 before one
+# rounding to FP32.  The one source of difference is the bottom matrix, which the two sides
+# build independently (entries equal to about 1e-16 relative): a bottom value could round to
+# the neighbouring binary32 number, an event of probability ~1e-9 per value, so these seeded
+# cases are expected to be exact.  Cases: half-sweeps throughout (the default for levels
+# below 256^3), the fused sweep on every level but the bottom, and the fused sweep with the
+# one-launch coarse cycle switched off (fused sweeps down to 4^3).
+
+MIXED_ITER_CASES = [(mg.MG_SMOOTH_AUTO, 0), (mg.MG_SMOOTH_FUSED, 0), (mg.MG_SMOOTH_FUSED, -1)]
+
+
+@pytest.mark.parametrize("smoother,coarse", MIXED_ITER_CASES)
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (0, 1, 1)])
+def test_mixed_iterates_match_oracle_bitwise(gctx, orc, smoother, coarse, periodic):
+    n, mb = 32, (16, 16, 16)
+    dom = (n - 1,) * 3
+    rhs = inputs.rng(46).standard_normal((n, n, n))
+    if all(periodic):
+        rhs = inputs.remove_mean(rhs)
+    ba, _ = _ba(gctx, dom, mb)
+    fr = gu.dense_fab(gctx, ba, rhs, 1)
+    boxes = orc.chop(Z3, dom, mb)
+    for k in (1, 2, 3):
+        fp = mg.mg_fab_alloc(gctx, ba, 1, 2)
+        opt = mg.make_options(precision=mg.MG_PREC_MIXED, fixed_vcycles=k, smoother=smoother,
+                              coarse_cells=coarse)
+        res = mg.mg_solve(gctx, fr, fp, mg.make_bc(periodic), 1e-10, opt)
+        phi = gu.fab_dense(gctx, fp, rhs.shape)
+        mg.mg_fab_free(gctx, fp)
+        o_phi, st, vc, _ = orc.solve(Z3, dom, periodic, boxes, 1.0 / n, rhs, fixed_vcycles=k,
+                                     mixed=True)
+        assert res.status == mg.MG_OK and res.vcycles == vc == k
+        assert np.array_equal(phi, o_phi), (k, np.abs(phi - o_phi).max())
+    mg.mg_fab_free(gctx, fr)
+
+
+def test_mixed_iterates_match_oracle_at_64(gctx, orc):
+    """The mixed form at 64^3 (Gaussian blobs, Dirichlet, 8 boxes): three outer iterations
+    equal the oracle's bit for bit, and the converged answer meets 1e-10."""
+    n, mb = 64, (32, 32, 32)
+    dom = (n - 1,) * 3
+    rhs = inputs.gaussian_blobs(n, seed=5)
+    ba, _ = _ba(gctx, dom, mb)
+    fr = gu.dense_fab(gctx, ba, rhs, 1)
+    fp = mg.mg_fab_alloc(gctx, ba, 1, 2)
+    res = mg.mg_solve(gctx, fr, fp, mg.make_bc((0, 0, 0)), 1e-10,
+                      mg.make_options(precision=mg.MG_PREC_MIXED, fixed_vcycles=3))
+    phi = gu.fab_dense(gctx, fp, rhs.shape)
+    mg.mg_fab_free(gctx, fp)
+    mg.mg_fab_free(gctx, fr)
+    o_phi, st, vc, _ = orc.solve(Z3, dom, (0, 0, 0), orc.chop(Z3, dom, mb), 1.0 / n, rhs,
+                                 fixed_vcycles=3, mixed=True)
+    assert res.vcycles == vc == 3
+    assert np.array_equal(phi, o_phi), np.abs(phi - o_phi).max()

@@ -49,17 +49,25 @@ def test_noalloc_norm_matches_mg_residual_on_two_calls():
             keep_r, pr, fr = _wrapped(ctx, ba, 0, rhs)
             mg.mg_fill_boundary(ctx, fp, bc)
             ref = mg.mg_residual(ctx, fp, fr, 0, h)
+            torch.cuda.synchronize()
+            # the device's free memory and the context pool are unchanged by the call (the
+            # first call's address lookup, made in the first trial, allocates nothing either)
+            free0, pool0 = torch.cuda.mem_get_info()[0], mg.mg_pool_info(ctx)[1]
             got = mg.mg_residual_norm_noalloc(dom_lo, dom_hi, boxes, pp, 1, pr, 0, h)
+            assert torch.cuda.mem_get_info()[0] == free0 and mg.mg_pool_info(ctx)[1] == pool0
             assert got == ref
             norms.append(got)
+            if trial == 1:
+                # beyond the maximum: rejected before any launch (the buffers passed are the
+                # live ones of this trial, so even a launch could not read outside them)
+                too_many = [(i, 0, 0, i, 0, 0) for i in range(1025)]
+                with pytest.raises(mg.MgError) as e:
+                    mg.mg_residual_norm_noalloc((0, 0, 0), (1024, 0, 0), too_many, pp, 1, pr, 0, 1.0)
+                assert e.value.code == mg.MG_EINVAL
             mg.mg_fab_free(ctx, fp)
             mg.mg_fab_free(ctx, fr)
             torch.cuda.synchronize()
             del keep_p, keep_r
         assert norms[1] < 1e-2 * norms[0]
-        too_many = [(i, 0, 0, i, 0, 0) for i in range(1025)]
-        with pytest.raises(mg.MgError) as e:
-            mg.mg_residual_norm_noalloc((0, 0, 0), (1024, 0, 0), too_many, 256, 1, 256, 0, 1.0)
-        assert e.value.code == mg.MG_EINVAL
     finally:
         mg.mg_finalize(ctx)
