@@ -1,22 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 multigrid Poisson path; prints ONE JSON line on rank 0.
 
-Default workload (dirichlet256): 256^3 homogeneous-Dirichlet FP64 Poisson problem split into
-64 boxes of 64^3, rhs = seeded N(0,1) smoothed by one damped-Jacobi pass, V(2,2) red-black
+Headline (dirichlet256): 256^3 homogeneous-Dirichlet FP64 Poisson problem split into 64
+boxes of 64^3, rhs = seeded N(0,1) smoothed by one damped-Jacobi pass, V(2,2) red-black
 Gauss-Seidel cycles to ||rhs - A phi||_inf <= 1e-10 ||rhs||_inf.  One step = one complete
 solve (phi reset to 0, then mg_solve) with rhs already resident in HBM.  `value` is solves/s
 over all ranks (each rank solves its own replica: this solve is not sharded across GPUs).
 
+On one GPU the same line also carries the other workloads as sub-objects, each with its own
+clock record: mixed512 (512^3, FP32 inner / FP64 outer, against the FP64 solve), batched512
+(512 independent solves packed into shared launches, mixed and FP64, against FP64 one at a
+time), serving (5000 Poisson arrivals whose data lives in host memory, through
+mg_submit_host, with latency percentiles and capacity, against a one-solve-at-a-time FP64
+server), fill (the ghost-fill microbench, fused against one launch per copy tag), triad
+(the STREAM triad of the paper's Sec. 3.1-3.2, per-box launches against one launch) and the
+measured FP64 rate that the FP64 kernels' roofline uses.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload dirichlet256|periodic64|mixed512|batched512|serving|fill]
-                    [--kernels-only] [--no-cpu-baseline]
+                    [--workload dirichlet256|periodic64|mixed512|batched512|serving|fill|triad]
+                    [--headline-only] [--kernels-only] [--no-cpu-baseline]
 
-Other workloads: mixed512 (512^3, FP32 inner / FP64 outer, against the FP64 solve),
-batched512 (512 independent solves packed into shared launches), serving (5000 Poisson
-arrivals through mg_submit/mg_poll, with latency percentiles and capacity, against a
-one-solve-at-a-time FP64 server), fill (the ghost-fill microbench, fused against one launch
-per copy tag).
-
+`--workload X` prints X's line alone; `--headline-only` skips the sub-objects.
 `--impl reference` times the CPU oracle (the plain FP64 restatement under oracle/) on this
 machine's host cores on the same workload, one V-cycle per step, extrapolated to a solve.
 """
@@ -263,7 +267,8 @@ def run_ours(args, wl_name):
     kt = kernel_timings(ctx, stream, ba, fp, fr, bc, h, cells, box)
     if sweep_n:
         kt["rbgs_half_f64_in_solve"] = sweep_ms / sweep_n / 1e3
-    roof = roofline(kt, wl_name, prec == mg.MG_PREC_F64, clocks, sweep_n)
+    fp64 = measure_fp64_peak(stream, local)
+    roof = roofline(kt, wl_name, prec == mg.MG_PREC_F64, fp64, sweep_n)
 
     # ---- end to end through the C ABI with host buffers
     e2e_steps = max(1, min(args.steps, 5))
@@ -294,12 +299,14 @@ def run_ours(args, wl_name):
         "latency_ms": {"p50": round(statistics.median(per), 3),
                        "p99": round(float(np.percentile(per, 99)), 3)},
         "vcycles": vcycles, "rel_resid": results[-1].rel_resid,
-        "cell_updates_per_s": round(cells * vcycles * (2 * (opt.nu1 + opt.nu2)) / (total_ms / args.steps / 1e3), 1),
+        "cell_updates_per_s": round(cells * vcycles * (opt.nu1 + opt.nu2) / (total_ms / args.steps / 1e3), 1),
+        "cell_updates": "finest level only: nu1 + nu2 = 4 updates per cell per V-cycle",
         "roofline": roof,
         "e2e": {"value": round(world * e2e_steps / t_e2e, 3), "unit": "solves/s",
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "fp64_peak": fp64,
     }
     if wl_name == "periodic64":
         # error against the continuous solution prod sin(2 pi x_d) (second order in h; the
@@ -334,6 +341,16 @@ def run_ours(args, wl_name):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl_name, vcycles)
     mg.mg_finalize(ctx)
+    del fr, fp
+    torch.cuda.empty_cache()
+    if wl_name == "dirichlet256" and world == 1 and not args.headline_only:
+        # the other workloads on this GPU, each with its own clock record
+        for key, fn in (("mixed512", sub_mixed512), ("batched512", sub_batched),
+                        ("serving", sub_serving), ("fill", sub_fill), ("triad", sub_triad)):
+            t = time.perf_counter()
+            line[key] = fn(args)
+            line[key]["wall_s"] = round(time.perf_counter() - t, 1)
+            torch.cuda.empty_cache()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -341,8 +358,6 @@ def run_ours(args, wl_name):
         print(json.dumps(line), flush=True)
 
 
-FP64_LANES_PER_SM_CLK = 2      # GB300 FP64 pipe: lane-operations per SM per clock
-N_SM = 152
 FP64_INST_PER_UPDATE = 7       # 5 DADD (neighbour sum) + 1 DFMA + 1 DMUL
 FP64_INST_PER_RESIDUAL = 7     # 5 DADD + 2 DFMA
 
@@ -358,6 +373,37 @@ def _time(stream, fn, reps):
     b.record(stream)
     stream.synchronize()
     return a.elapsed_time(b) / reps / 1e3
+
+
+def measure_fp64_peak(stream, device_index, target_ms=40.0):
+    """The device's FP64 issue rate (G lane-ops/s): the library's FMA-chain probe, sized to
+    run about target_ms, best of 5 timed launches (CUDA events on `stream`) after 3
+    warm-ups, with the SM clock sampled meanwhile."""
+    import torch
+    from paper_2403_12179_gb300 import mg
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = 200
+    a.record(stream)
+    ops = mg.mg_calib_fp64(stream, iters)
+    b.record(stream)
+    stream.synchronize()
+    iters = max(1, int(iters * target_ms / max(a.elapsed_time(b), 1e-3)))
+    for _ in range(3):
+        mg.mg_calib_fp64(stream, iters)
+    stream.synchronize()
+    clk = Clocks(device_index)
+    best = 0.0
+    for _ in range(5):
+        a.record(stream)
+        ops = mg.mg_calib_fp64(stream, iters)
+        b.record(stream)
+        stream.synchronize()
+        best = max(best, ops / (a.elapsed_time(b) / 1e3) / 1e9)
+    clocks = clk.stop()
+    return {"value": round(best, 1), "unit": "G FP64 lane-ops/s",
+            "how": f"mg_calib_fp64: {ops} DFMA lane-ops per launch (8 independent chains per "
+                   "thread, 8 blocks of 256 threads per SM), best of 5 launches, CUDA events",
+            "clocks": clocks}
 
 
 def kernel_timings(ctx, stream, ba, fp, fr, bc, h, cells, box, reps=40):
@@ -390,11 +436,10 @@ def kernel_timings(ctx, stream, ba, fp, fr, bc, h, cells, box, reps=40):
     return out
 
 
-def roofline(kt, wl_name, f64, clocks, in_solve_launches=0):
+def roofline(kt, wl_name, f64, fp64, in_solve_launches=0):
     peaks, src = load_peaks()
     cells = WORKLOADS[wl_name]["n"] ** 3
-    sm_mhz = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = FP64_LANES_PER_SM_CLK * N_SM * sm_mhz * 1e6 / 1e9      # G lane-ops/s
+    fp64_peak = fp64["value"]                                          # G lane-ops/s, measured
     hbm = peaks["hbm_gbs"]
     # the FP64 half-sweep's duration inside the timed solves when measured there, else the
     # separate timing loop
@@ -412,8 +457,15 @@ def roofline(kt, wl_name, f64, clocks, in_solve_launches=0):
         "rbgs_fused_f32": {"launch_us": round(kt["rbgs_fused_f32"] * 1e6, 2),
                            "hbm_frac": round(12 * cells / kt["rbgs_fused_f32"] / 1e9 / hbm, 4)},
         "rbgs_half_f32": {"launch_us": round(kt["rbgs_half_f32"] * 1e6, 2),
-                          "hbm_frac": round(8 * cells / kt["rbgs_half_f32"] / 1e9 / hbm, 4)},
+                          "hbm_frac": round(8 * cells / kt["rbgs_half_f32"] / 1e9 / hbm, 4),
+                          # the colours interleave within every 32-byte sector, so a half-sweep
+                          # reads all of phi and rhs and writes back all of phi: 12 B/cell
+                          "dram_min_frac": round(12 * cells / kt["rbgs_half_f32"] / 1e9 / hbm, 4)},
     }
+    extra["note"] = ("the FP64 kernels (half-sweep, residual) are bound by GB300's FP64 issue "
+                     "rate, measured by fp64_peak: at 100% of it a half-sweep moves about 42% of "
+                     "the HBM copy peak, so the 70%-of-HBM target applies to the FP32 kernels "
+                     "(rbgs_fused_f32, rbgs_half_f32) only")
     if f64:
         ach = half_ops / t / 1e9
         where = (f"average of {in_solve_launches} launches inside the timed solves (CUDA events "
@@ -422,7 +474,11 @@ def roofline(kt, wl_name, f64, clocks, in_solve_launches=0):
                 "bound": "alu", "measured": where,
                 "achieved": round(ach, 1), "peak": round(fp64_peak, 1),
                 "unit": "G FP64 lane-ops/s", "frac": round(ach / fp64_peak, 4),
-                "peak_source": f"derived: {FP64_LANES_PER_SM_CLK} FP64 lanes/clk/SM x {N_SM} SMs x {sm_mhz:.0f} MHz",
+                "peak_source": "measured: mg_calib_fp64 (independent DFMA chains on every SM, "
+                               "CUDA events; see fp64_peak)",
+                "hbm": {"achieved_gbs": round(16 * cells / t / 1e9, 1), "peak": hbm,
+                        "frac": round(16 * cells / t / 1e9 / hbm, 4),
+                        "algorithmic_bytes_per_launch": 16 * cells},
                 "algorithmic_ops_per_launch": half_ops,
                 "traffic": roofline_traffic("rbgs_half_f64", wl_name), "kernels": extra}
     t = kt["rbgs_fused_f32"]
@@ -473,11 +529,103 @@ def _fab_to_dense(ctx, fab, shape, stream=None):
     return out
 
 
-def run_batched(args):
-    """512 independent periodic problems (edges from {32,48,64,96,128}, 32^3 boxes): all
-    packed into one launch per V-cycle stage, FP64 and mixed; against the same problems
-    solved one at a time with mg_solve (FP64)."""
+def _events(n):
+    import torch
+    return ([torch.cuda.Event(enable_timing=True) for _ in range(n)],
+            [torch.cuda.Event(enable_timing=True) for _ in range(n)])
+
+
+def sub_mixed512(args, steps=5, warmup=2):
+    """512^3 Dirichlet, 64 boxes of 128^3, Gaussian blobs: the mixed-precision solve (FP32
+    inner V-cycle, FP64 outer residual / correction / bottom) against the plain FP64 solve of
+    the same problem, both timed with CUDA events on the solve stream (L2 flushed before each
+    solve, outside the events); the difference of the two answers against the bound two
+    converged answers obey (P7); the FP32 smoother kernels at this size."""
     import numpy as np
+    import torch
+    from paper_2403_12179_gb300 import mg
+    wl = WORKLOADS["mixed512"]
+    n, box = wl["n"], wl["box"]
+    cells = n ** 3
+    ctx = mg.mg_init(0)
+    stream = torch.cuda.Stream()
+    mg.mg_set_stream(ctx, stream)
+    ba = mg.mg_box_array_create(ctx, (0, 0, 0), (n - 1,) * 3, (box,) * 3)
+    rhs_np = make_rhs(wl)
+    rhs_max = float(np.abs(rhs_np).max())
+    fr = mg.mg_fab_alloc(ctx, ba, 1, 1)
+    d = torch.from_numpy(rhs_np).cuda()
+    mg.mg_fab_copy_from_dense(ctx, fr, d.data_ptr(), False, stream)
+    stream.synchronize()
+    del d, rhs_np
+    bc = mg.make_bc(wl["periodic"])
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    out = {"workload": wl["desc"], "cells": cells, "boxes": (n // box) ** 3}
+    phis = {}
+    for name, prec in (("mixed", mg.MG_PREC_MIXED), ("f64", mg.MG_PREC_F64)):
+        fp = mg.mg_fab_alloc(ctx, ba, 1, 2)
+        opt = mg.make_options(precision=prec)
+
+        def solve():
+            mg.mg_fab_set_val(ctx, fp, 0.0, True, stream)
+            return mg.mg_solve(ctx, fr, fp, bc, 1e-10, opt)
+        for _ in range(warmup):
+            solve()
+        k = steps if name == "mixed" else max(2, steps // 2)
+        e0, e1 = _events(k)
+        clk = Clocks(torch.cuda.current_device())
+        res = []
+        with torch.cuda.stream(stream):
+            for i in range(k):
+                flush.zero_()
+                e0[i].record(stream)
+                res.append(solve())
+                e1[i].record(stream)
+        stream.synchronize()
+        clocks = clk.stop()
+        ms = [e0[i].elapsed_time(e1[i]) for i in range(k)]
+        assert all(r.status == 0 and r.rel_resid <= 1e-10 for r in res), f"{name} solve failed"
+        out[name] = {"solves_per_s": round(1e3 / statistics.median(ms), 3),
+                     "ms_per_solve": round(statistics.median(ms), 3), "steps": k,
+                     "outer_iterations" if name == "mixed" else "vcycles": res[-1].vcycles,
+                     "rel_resid": res[-1].rel_resid, "clocks": clocks}
+        phis[name] = _fab_to_dense(ctx, fp, (n,) * 3, stream)
+        mg.mg_fab_free(ctx, fp, stream)
+    diff = float((phis["mixed"] - phis["f64"]).abs().max())
+    del phis
+    out["mixed_speedup_vs_f64"] = round(out["f64"]["ms_per_solve"] / out["mixed"]["ms_per_solve"], 3)
+    out["max_abs_diff_vs_f64"] = diff
+    out["p7_bound"] = 2 * 0.06 * 1e-10 * rhs_max
+    # the FP32 smoother kernels on this level, back to back on the solve stream
+    peaks, _ = load_peaks()
+    hbm = peaks["hbm_gbs"]
+    a32 = mg.mg_fab_alloc(ctx, ba, 1, 2, mg.MG_F32)
+    b32 = mg.mg_fab_alloc(ctx, ba, 1, 2, mg.MG_F32)
+    r32 = mg.mg_fab_alloc(ctx, ba, 1, 1, mg.MG_F32)
+    mg.mg_fab_set_val(ctx, r32, 1.0, True, stream)
+    mg.mg_fill_boundary(ctx, a32, bc, stream)
+    mg.mg_fill_boundary(ctx, b32, bc, stream)
+    pair = (a32, b32)
+    h = 1.0 / n
+    t_f = _time(stream, lambda k: mg.mg_smooth_fused(ctx, pair[k & 1], r32, pair[(k + 1) & 1], bc, h, stream), 20)
+    t_h = _time(stream, lambda k: mg.mg_smooth(ctx, a32, r32, bc, h, (k & 1) | mg.MG_SMOOTH_DIRECT_READS, stream), 20)
+    out["kernels"] = {
+        "rbgs_fused_f32": {"launch_us": round(t_f * 1e6, 1), "gbs": round(12 * cells / t_f / 1e9, 1),
+                           "hbm_frac": round(12 * cells / t_f / 1e9 / hbm, 4),
+                           "algorithmic_bytes_per_cell": 12},
+        "rbgs_half_f32": {"launch_us": round(t_h * 1e6, 1), "gbs": round(8 * cells / t_h / 1e9, 1),
+                          "hbm_frac": round(8 * cells / t_h / 1e9 / hbm, 4),
+                          "dram_min_frac": round(12 * cells / t_h / 1e9 / hbm, 4),
+                          "algorithmic_bytes_per_cell": 8}}
+    mg.mg_finalize(ctx)
+    return out
+
+
+def sub_batched(args, steps=3, warmup=1):
+    """512 independent periodic problems (edges from {32,48,64,96,128}, 32^3 boxes): all
+    packed into one launch per V-cycle stage, mixed and FP64; against the same problems solved
+    one at a time with mg_solve (FP64).  Times are host wall times around the synchronous
+    calls (inputs resident)."""
     import torch
     from paper_2403_12179_gb300 import inputs, mg
     probs = inputs.batched_periodic(args.count, seed=4)
@@ -498,17 +646,20 @@ def run_batched(args):
     def batch(prec):
         for f in fp:
             mg.mg_fab_set_val(ctx, f, 0.0, True, stream)
+        stream.synchronize()
         t = time.perf_counter()
         res = mg.mg_solve_batch(ctx, fr, fp, bcs, 1e-10, mg.make_options(precision=prec))
         dt = time.perf_counter() - t
         assert all(r.status == 0 and r.rel_resid <= 1e-10 for r in res), "batched solve failed"
         return dt, res
 
-    out, vcs = {}, {}
+    out, vcs, clocks = {}, {}, {}
     for name, prec in (("mixed", mg.MG_PREC_MIXED), ("f64", mg.MG_PREC_F64)):
-        for _ in range(max(1, args.warmup)):
+        for _ in range(max(1, warmup)):
             batch(prec)
-        runs = [batch(prec) for _ in range(args.steps)]
+        clk = Clocks(torch.cuda.current_device())
+        runs = [batch(prec) for _ in range(steps)]
+        clocks[name] = clk.stop()
         out[name] = statistics.median(r[0] for r in runs)
         vcs[name] = [r.vcycles for r in runs[-1][1]]
     phis64 = [_fab_to_dense(ctx, f, sh, stream) for f, sh in zip(fp, shapes)]
@@ -516,39 +667,51 @@ def run_batched(args):
     diff = 0.0
     for f, sh, p64 in zip(fp, shapes, phis64):
         pm = _fab_to_dense(ctx, f, sh, stream)
-        d = (pm - pm.mean()) - (p64 - p64.mean())
-        diff = max(diff, float(d.abs().max()))
-    # one solve at a time, FP64, same problems
-    seq = []
+        dd = (pm - pm.mean()) - (p64 - p64.mean())
+        diff = max(diff, float(dd.abs().max()))
+    del phis64
+    # one solve at a time, FP64, same problems (hierarchies and graphs built beforehand)
     for f in fp:
         mg.mg_fab_set_val(ctx, f, 0.0, True, stream)
-    for a, b in zip(fr, fp):                       # warm: hierarchies and graphs exist
+    for a, b in zip(fr, fp):
         mg.mg_solve(ctx, a, b, bcs[0], 1e-10)
     for f in fp:
         mg.mg_fab_set_val(ctx, f, 0.0, True, stream)
     stream.synchronize()
+    clk = Clocks(torch.cuda.current_device())
     t = time.perf_counter()
     for a, b in zip(fr, fp):
         r = mg.mg_solve(ctx, a, b, bcs[0], 1e-10)
-        seq.append(r.vcycles)
+        assert r.status == 0
     t_seq = time.perf_counter() - t
+    clocks["f64_one_at_a_time"] = clk.stop()
+    mg.mg_finalize(ctx)
     n = len(probs)
-    line = {"metric": f"solves/s, {n} batched periodic problems to 1e-10 (mixed precision)",
-            "value": round(n / out["mixed"], 2), "unit": "solves/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(out["mixed"] * 1e3, 2),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 inner / f64 outer", "data": "synthetic",
-            "config": {"workload": "batched512", "problems": n, "cells": cells,
-                       "edges": "32/48/64/96/128 (seed 4)", "box": 32},
+    line = {"problems": n, "cells": cells, "edges": "32/48/64/96/128 (seed 4)", "box": 32,
+            "mixed_batched_solves_per_s": round(n / out["mixed"], 2),
             "f64_batched_solves_per_s": round(n / out["f64"], 2),
             "f64_one_at_a_time_solves_per_s": round(n / t_seq, 2),
+            "mixed_batched_vs_f64_one_at_a_time": round(t_seq / out["mixed"], 3),
+            "ms_per_batch": {"mixed": round(out["mixed"] * 1e3, 2), "f64": round(out["f64"] * 1e3, 2)},
             "cell_updates_per_s_mixed": round(sum(pb.n ** 3 * 4 * v for pb, v in
                                                   zip(probs, vcs["mixed"])) / out["mixed"], 1),
             "cell_updates": "finest level: 4 per cell per V-cycle (V(2,2)), each problem's own count",
-            "max_abs_diff_mixed_vs_f64_mod_const": diff}
-    mg.mg_finalize(ctx)
+            "max_abs_diff_mixed_vs_f64_mod_const": diff, "steps": steps, "clocks": clocks}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_batched(probs)
+        line["cpu_baseline"] = cpu_baseline_batched(probs, budget_s=6.0)
+    return line
+
+
+def run_batched(args):
+    sub = sub_batched(args, steps=args.steps, warmup=args.warmup)
+    n = sub["problems"]
+    line = {"metric": f"solves/s, {n} batched periodic problems to 1e-10 (mixed precision)",
+            "value": sub["mixed_batched_solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sub["ms_per_batch"]["mixed"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer",
+            "data": "synthetic", "config": {"workload": "batched512"}}
+    line.update(sub)
     print(json.dumps(line), flush=True)
 
 
@@ -574,114 +737,233 @@ def cpu_baseline_batched(probs, budget_s=10.0):
                       f"in {el:.1f} s"}
 
 
-def run_serving(args):
-    """Poisson arrivals (200/s), edges {32,64,128,256} p={.4,.3,.2,.1}, periodic/Dirichlet,
-    32^3 or 64^3 boxes: real-time replay through mg_submit/mg_poll (mixed precision,
-    continuous batching), against a one-at-a-time FP64 server (mg_solve in arrival order,
-    latencies from measured service times).  Both are warmed up with one request per shape.
-    Capacity: the mixed server with every request queued at once; the FP64 server's is one
-    over its mean service time."""
+class HostInputs:
+    """Draws the serving requests' right-hand sides into pinned host memory ahead of their
+    arrival, in arrival order, on a pool of threads (NumPy releases the GIL while it draws),
+    keeping at most `budget` bytes of drawn-but-unsubmitted data.  Buffers are recycled per
+    size; `get(i)` waits for request i's rhs; `put(a)` returns a buffer to its pool."""
+
+    def __init__(self, reqs, threads, budget, start=0, stop=None):
+        import threading
+        self.reqs = reqs
+        self.stop_at = len(reqs) if stop is None else stop
+        self.next = start
+        self.budget = budget
+        self.ahead = 0
+        self.mu = threading.Lock()
+        self.cv = threading.Condition(self.mu)
+        self.ready = {}
+        self.free = {}
+        self.quit = False
+        self.threads = [threading.Thread(target=self._work, daemon=True) for _ in range(threads)]
+        for t in self.threads:
+            t.start()
+
+    def buffer(self, n):
+        import torch
+        with self.mu:
+            lst = self.free.get(n)
+            if lst:
+                return lst.pop()
+        return torch.empty((n, n, n), dtype=torch.float64, pin_memory=True)
+
+    def put(self, a):
+        with self.mu:
+            self.free.setdefault(a.shape[0], []).append(a)
+
+    def _work(self):
+        while True:
+            with self.cv:
+                while not self.quit and self.next < self.stop_at and self.ahead >= self.budget:
+                    self.cv.wait()
+                if self.quit or self.next >= self.stop_at:
+                    return
+                i = self.next
+                self.next += 1
+                nb = self.reqs[i].n ** 3 * 8
+                self.ahead += nb
+            buf = self.buffer(self.reqs[i].n)
+            self.reqs[i].rhs_into(buf.numpy())
+            with self.cv:
+                self.ready[i] = buf
+                self.cv.notify_all()
+
+    def get(self, i):
+        with self.cv:
+            while i not in self.ready:
+                self.cv.wait()
+            buf = self.ready.pop(i)
+            self.ahead -= buf.numel() * 8
+            self.cv.notify_all()
+            return buf
+
+    def wait_ahead(self, fraction=0.9):
+        with self.cv:
+            while self.ahead < fraction * self.budget and self.next < self.stop_at:
+                self.cv.wait()
+
+    def close(self):
+        with self.cv:
+            self.quit = True
+            self.cv.notify_all()
+        for t in self.threads:
+            t.join()
+
+
+def sub_serving(args):
+    """Serving: Poisson arrivals (200/s) of requests with edges {32,64,128,256}
+    (p = .4/.3/.2/.1), periodic / Dirichlet, 32^3 or 64^3 boxes, rhs = PCG64 N(0,1) per request
+    (inputs.serving_requests).  Each request's data lives in pinned host memory, drawn ahead
+    of its arrival by a pool of host threads; at its arrival time it is submitted with
+    mg_submit_host, so its latency (submit -> answer back in host memory) includes the copy
+    in, the queueing, the shared V-cycle steps and the copy out, and the scheduler admits it
+    only when the pool holds its whole hierarchy (fine level included).  Latencies are taken
+    from the scheduled arrival.  Against it: one solve at a time in FP64 (mg_solve on fabs
+    reused per shape, copy in / solve / copy out per request, service times measured
+    back to back, latencies from the arrival times through a FIFO queue).  Capacity: a burst
+    of the first requests queued at once (as many as fit in a pinned budget)."""
     import threading
     import numpy as np
     import torch
     from paper_2403_12179_gb300 import inputs, mg
     reqs = inputs.serving_requests(args.requests, seed=6)
-    ctx = mg.mg_init(0)
-    fabs = []
-    gen = torch.Generator(device="cuda")
-    for rq in reqs:
-        ba = mg.mg_box_array_create(ctx, (0, 0, 0), (rq.n - 1,) * 3, (rq.box,) * 3)
-        gen.manual_seed(rq.seed)
-        d = torch.randn((rq.n,) * 3, dtype=torch.float64, device="cuda", generator=gen)
-        if rq.periodic:
-            d -= d.mean()
-        fr = _dense_to_fab(ctx, ba, d, 1)
-        fp = mg.mg_fab_alloc(ctx, ba, 1, 2)
-        fabs.append((fr, fp, mg.make_bc((1, 1, 1) if rq.periodic else (0, 0, 0))))
-    torch.cuda.synchronize()
+    N = len(reqs)
+    cores = os.cpu_count() or 4
+    gen_threads = max(2, cores - 4)
+    budget = 4 << 30
     opt = mg.make_options(precision=mg.MG_PREC_MIXED)
     shapes = sorted({(rq.n, rq.box, rq.periodic) for rq in reqs})
-
-    def warm_fabs(ctx, n, box, per):
-        ba = mg.mg_box_array_create(ctx, (0, 0, 0), (n - 1,) * 3, (box,) * 3)
-        d = torch.randn((n,) * 3, dtype=torch.float64, device="cuda", generator=gen)
-        if per:
-            d -= d.mean()
-        return _dense_to_fab(ctx, ba, d, 1), mg.mg_fab_alloc(ctx, ba, 1, 2), \
-            mg.make_bc((1, 1, 1) if per else (0, 0, 0))
-
-    # warm-up (untimed): one request of every shape, so that one-time work (fused-sweep
-    # autotuning, first launches) is not part of the replay
-    gen.manual_seed(7)
-    warm = [warm_fabs(ctx, *sh) for sh in shapes]
-    for t in [mg.mg_submit(ctx, fr, fp, bc, 1e-10, opt) for fr, fp, bc in warm]:
+    bcs = {p: mg.make_bc((1, 1, 1) if p else (0, 0, 0)) for p in (True, False)}
+    ctx = mg.mg_init(0)
+    # warm-up (untimed): one request of every shape through the same path
+    warm = []
+    for k, (n, b, p) in enumerate(shapes):
+        r = inputs.Request(0.0, n, p, b, 77 + k)
+        ra = torch.from_numpy(r.rhs()).pin_memory()
+        pa = torch.empty_like(ra).pin_memory()
+        warm.append((ra, pa, mg.mg_submit_host(ctx, (0, 0, 0), (n - 1,) * 3, (b,) * 3, bcs[p],
+                                               ra.data_ptr(), pa.data_ptr(), False, 1e-10, opt)))
+    for _, _, t in warm:
         mg.mg_poll(ctx, t, -1)
-    for fr, fp, _ in warm:
-        mg.mg_fab_free(ctx, fr)
-        mg.mg_fab_free(ctx, fp)
+    del warm
     stats0 = mg.mg_server_stats_get(ctx)
-    results = [None] * len(reqs)
-    tickets = [None] * len(reqs)
+    gen = HostInputs(reqs, gen_threads, budget)
+    gen.wait_ahead(0.9)
+    # a few sampled Dirichlet requests of edge <= 64 keep their answer for the oracle check
+    sample = [i for i, rq in enumerate(reqs) if not rq.periodic and rq.n <= 64][:: max(1, N // 400)][:10]
+    results = [None] * N
+    tickets = [None] * N
+    phis = [None] * N
+    rhss = [None] * N
+    lag = np.zeros(N)
+    t_sub = np.zeros(N)
+    kept = {}
     ready = threading.Semaphore(0)
 
     def poller():
-        for i in range(len(reqs)):
+        for i in range(N):
             ready.acquire()
             rc, r = mg.mg_poll(ctx, tickets[i], -1)
             results[i] = r
+            if i in sample:
+                kept[i] = phis[i].numpy().copy()
+            gen.put(rhss[i])
+            gen.put(phis[i])
+            rhss[i] = phis[i] = None
 
     th = threading.Thread(target=poller)
+    clk = Clocks(torch.cuda.current_device())
     th.start()
     t0 = time.perf_counter()
     for i, rq in enumerate(reqs):
+        a = gen.get(i)
+        ph = gen.buffer(rq.n)
         delay = t0 + rq.t_arrive - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        fr, fp, bc = fabs[i]
-        tickets[i] = mg.mg_submit(ctx, fr, fp, bc, 1e-10, opt)
+        rhss[i], phis[i] = a, ph
+        t_sub[i] = time.perf_counter()
+        lag[i] = t_sub[i] - (t0 + rq.t_arrive)
+        tickets[i] = mg.mg_submit_host(ctx, (0, 0, 0), (rq.n - 1,) * 3, (rq.box,) * 3,
+                                       bcs[rq.periodic], a.data_ptr(), ph.data_ptr(), False,
+                                       1e-10, opt)
         ready.release()
     th.join()
-    wall = max(r.t_end for r in results) - min(r.t_start for r in results)
-    lat = np.array([r.seconds for r in results]) * 1e3
+    clocks = clk.stop()
+    gen.close()
+    # latency from the scheduled arrival: the library's submit -> done, plus the submission lag
+    lat = np.array([r.seconds for r in results]) + np.maximum(lag, 0.0)
+    wall = max((t_sub[i] - t0) + results[i].seconds for i in range(N)) - reqs[0].t_arrive
     ok = all(r.status == 0 and r.rel_resid <= 1e-10 for r in results)
     stats = mg.mg_server_stats_get(ctx)
     stats = {k: (v - stats0[k] if k != "max_active" else v) for k, v in stats.items()}
-    # capacity: the same requests all queued at once (phi reset to the zero guess); the
-    # scheduler admits them as the pool allows
-    for _, fp, _ in fabs:
-        mg.mg_fab_set_val(ctx, fp, 0.0, True)
-    torch.cuda.synchronize()
+    # capacity: a burst of the first M requests queued at once (rhs drawn beforehand; the
+    # answer is written over the rhs buffer, which the scheduler has copied in by then)
+    cap_budget = 6 << 30
+    M, tot = 0, 0
+    while M < N and tot + reqs[M].n ** 3 * 8 <= cap_budget:
+        tot += reqs[M].n ** 3 * 8
+        M += 1
+    bufs = []
+    for i in range(M):
+        b = torch.empty((reqs[i].n,) * 3, dtype=torch.float64, pin_memory=True)
+        reqs[i].rhs_into(b.numpy())
+        bufs.append(b)
     t = time.perf_counter()
-    tk = [mg.mg_submit(ctx, fr, fp, bc, 1e-10, opt) for fr, fp, bc in fabs]
+    tk = [mg.mg_submit_host(ctx, (0, 0, 0), (reqs[i].n - 1,) * 3, (reqs[i].box,) * 3,
+                            bcs[reqs[i].periodic], bufs[i].data_ptr(), bufs[i].data_ptr(), False,
+                            1e-10, opt) for i in range(M)]
     burst = [mg.mg_poll(ctx, x, -1)[1] for x in tk]
-    cap = len(reqs) / (time.perf_counter() - t)
+    cap = M / (time.perf_counter() - t)
     ok = ok and all(r.status == 0 and r.rel_resid <= 1e-10 for r in burst)
+    del bufs
     mg.mg_finalize(ctx)
-    # one-at-a-time FP64 server on the same requests (warmed up the same way)
+    # oracle check of the sampled answers (mixed oracle solve; P7 bound of two converged
+    # answers on the Dirichlet unit cube)
+    import oracle
+    oracle.build()
+    worst = 0.0
+    for i in sample:
+        rq = reqs[i]
+        rhs = rq.rhs()
+        dom = (rq.n - 1,) * 3
+        o, st, _, _ = oracle.solve((0, 0, 0), dom, (0, 0, 0), oracle.chop((0, 0, 0), dom, (rq.box,) * 3),
+                                   1.0 / rq.n, rhs, mixed=True)
+        assert st == 0
+        worst = max(worst, float(np.abs(kept[i] - o).max()) / (2 * 0.06 * 1e-10 * float(np.abs(rhs).max())))
+    # one-at-a-time FP64 server on the same requests: fabs reused per shape, each request's
+    # rhs copied in from pinned memory, solved, answer copied out
     ctx = mg.mg_init(0)
-    gen.manual_seed(7)
-    for sh in shapes:
-        fr, fp, bc = warm_fabs(ctx, *sh)
-        mg.mg_solve(ctx, fr, fp, bc, 1e-10)
-        mg.mg_fab_free(ctx, fr)
-        mg.mg_fab_free(ctx, fp)
-    svc = []
+    stream = torch.cuda.Stream()
+    mg.mg_set_stream(ctx, stream)
+    fabs = {}
+    for (n, b, p) in shapes:
+        ba = mg.mg_box_array_create(ctx, (0, 0, 0), (n - 1,) * 3, (b,) * 3)
+        fabs[(n, b, p)] = (mg.mg_fab_alloc(ctx, ba, 1, 1), mg.mg_fab_alloc(ctx, ba, 1, 2))
+        r = inputs.Request(0.0, n, p, b, 77)
+        ra = torch.from_numpy(r.rhs()).pin_memory()
+        fr, fp = fabs[(n, b, p)]
+        mg.mg_fab_copy_from_dense(ctx, fr, ra.data_ptr(), True, stream)
+        mg.mg_solve(ctx, fr, fp, bcs[p], 1e-10)
+    gen = HostInputs(reqs, gen_threads, budget)
+    svc = np.zeros(N)
+    clk = Clocks(torch.cuda.current_device())
     for i, rq in enumerate(reqs):
-        ba = mg.mg_box_array_create(ctx, (0, 0, 0), (rq.n - 1,) * 3, (rq.box,) * 3)
-        gen.manual_seed(rq.seed)
-        d = torch.randn((rq.n,) * 3, dtype=torch.float64, device="cuda", generator=gen)
-        if rq.periodic:
-            d -= d.mean()
-        fr = _dense_to_fab(ctx, ba, d, 1)
-        fp = mg.mg_fab_alloc(ctx, ba, 1, 2)
-        bc = mg.make_bc((1, 1, 1) if rq.periodic else (0, 0, 0))
-        torch.cuda.synchronize()
+        a = gen.get(i)
+        ph = gen.buffer(rq.n)
+        fr, fp = fabs[(rq.n, rq.box, rq.periodic)]
         t = time.perf_counter()
-        r = mg.mg_solve(ctx, fr, fp, bc, 1e-10)
-        svc.append(time.perf_counter() - t)
+        mg.mg_fab_copy_from_dense(ctx, fr, a.data_ptr(), True, stream)
+        mg.mg_fab_set_val(ctx, fp, 0.0, True, stream)
+        r = mg.mg_solve(ctx, fr, fp, bcs[rq.periodic], 1e-10)
+        mg.mg_fab_copy_to_dense(ctx, fp, ph.data_ptr(), True, stream)
+        stream.synchronize()
+        svc[i] = time.perf_counter() - t
         ok = ok and r.status == 0
-        mg.mg_fab_free(ctx, fr)
-        mg.mg_fab_free(ctx, fp)
+        gen.put(a)
+        gen.put(ph)
+    clocks64 = clk.stop()
+    gen.close()
     mg.mg_finalize(ctx)
     end, lat64 = 0.0, []
     for rq, sv in zip(reqs, svc):
@@ -690,30 +972,44 @@ def run_serving(args):
         lat64.append((end - rq.t_arrive) * 1e3)
     lat64 = np.array(lat64)
     wall64 = end - reqs[0].t_arrive
-    n = len(reqs)
-    line = {"metric": f"served solves/s and latency, {n} Poisson-arrival requests at 200/s",
-            "value": round(n / wall, 2), "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 inner / f64 outer", "data": "synthetic (torch Philox rhs per request seed)",
-            "config": {"workload": "serving", "requests": n, "rate_per_s": 200,
-                       "warmup": f"one untimed request per shape ({len(shapes)} shapes) before the replay",
-                       "edges": "32/64/128/256 p=.4/.3/.2/.1", "bc": "periodic/Dirichlet 50/50",
-                       "box": "32 or 64"},
-            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2),
-                           "p99": round(float(np.percentile(lat, 99)), 2)},
-            "all_converged_to_1e-10": ok, "scheduler": stats,
-            "capacity_solves_per_s": round(cap, 2),
-            "f64_one_at_a_time": {"solves_per_s": round(n / wall64, 2),
+    return {"requests": N, "rate_per_s": 200, "edges": "32/64/128/256 p=.4/.3/.2/.1",
+            "bc": "periodic/Dirichlet 50/50", "box": "32 or 64", "precision": "mixed",
+            "data": "PCG64 N(0,1) per request (inputs.serving_requests), drawn into pinned "
+                    "host memory ahead of arrival; submitted with mg_submit_host",
+            "solves_per_s": round(N / wall, 2),
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)) * 1e3, 2),
+                           "p99": round(float(np.percentile(lat, 99)) * 1e3, 2),
+                           "includes": "copy in from host, queueing, V-cycle steps, copy out; "
+                                       "from the scheduled arrival"},
+            "submit_lag_ms": {"p50": round(float(np.percentile(lag, 50)) * 1e3, 3),
+                              "max": round(float(lag.max()) * 1e3, 3)},
+            "all_converged_to_1e-10": bool(ok), "scheduler": stats,
+            "capacity_solves_per_s": round(cap, 2), "capacity_burst_requests": M,
+            "oracle_check": {"requests": len(sample), "kind": "mixed oracle solve, Dirichlet, edge <= 64",
+                             "worst_diff_over_p7_bound": round(worst, 6), "pass": bool(worst <= 1.0)},
+            "f64_one_at_a_time": {"solves_per_s": round(N / wall64, 2),
                                   "capacity_solves_per_s": round(1.0 / float(np.mean(svc)), 2),
                                   "latency_ms": {"p50": round(float(np.percentile(lat64, 50)), 2),
                                                  "p99": round(float(np.percentile(lat64, 99)), 2)},
-                                  "mean_service_ms": round(float(np.mean(svc)) * 1e3, 3)}}
+                                  "mean_service_ms": round(float(np.mean(svc)) * 1e3, 3),
+                                  "clocks": clocks64},
+            "clocks": clocks}
+
+
+def run_serving(args):
+    sub = sub_serving(args)
+    line = {"metric": f"served solves/s and latency, {sub['requests']} Poisson-arrival requests at 200/s",
+            "value": sub["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner / f64 outer", "data": "synthetic",
+            "config": {"workload": "serving"}}
+    line.update(sub)
     print(json.dumps(line), flush=True)
 
 
-def run_fill(args):
+def sub_fill(args, reps=200):
     """FillBoundary microbench: 256^3 periodic, 64 boxes of 64^3, 4 FP64 components, 2 ghost
-    layers; one fill kernel per call."""
+    layers; one fill kernel per call, against one launch per copy tag."""
     import torch
     from paper_2403_12179_gb300 import inputs, mg
     ctx = mg.mg_init(0)
@@ -722,28 +1018,90 @@ def run_fill(args):
     fab = mg.mg_fab_alloc(ctx, ba, 4, 2)
     d = torch.from_numpy(inputs.fill_microbench(256, seed=3)).cuda()
     mg.mg_fab_copy_from_dense(ctx, fab, d.data_ptr(), False, stream)
+    stream.synchronize()
+    del d
     bc = mg.make_bc((1, 1, 1))
-    for _ in range(args.warmup):
+    for _ in range(3):
         mg.mg_fill_boundary(ctx, fab, bc, stream)
-    t = _time(stream, lambda k: mg.mg_fill_boundary(ctx, fab, bc, stream), args.steps * 10)
-    # the unfused form (one launch per copy tag), the paper's Sec. 3.2 comparison
-    t_unfused = _time(stream, lambda k: mg.mg_fill_boundary_unfused(ctx, fab, bc, stream), args.steps)
+    clk = Clocks(torch.cuda.current_device())
+    t = _time(stream, lambda k: mg.mg_fill_boundary(ctx, fab, bc, stream), reps)
+    t_unfused = _time(stream, lambda k: mg.mg_fill_boundary_unfused(ctx, fab, bc, stream), 5)
+    clocks = clk.stop()
     ntags = len(mg.mg_copy_tags(ctx, ba, bc, 2))
+    mg.mg_finalize(ctx)
     ghost = 64 * (68 ** 3 - 64 ** 3)
     nbytes = ghost * 4 * 8 * 2
     peaks, src = load_peaks()
     ach = nbytes / t / 1e9
-    line = {"metric": "FillBoundary time per fill (256^3, 64 boxes, 4 comps, 2 ghosts, periodic)",
-            "value": round(t * 1e6, 2), "unit": "us", "n_gpus": 1, "steps": args.steps * 10,
-            "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "fill", "ghost_cells": ghost, "bytes_per_fill": nbytes},
+    return {"us_per_fill": round(t * 1e6, 2), "ghost_cells": ghost, "bytes_per_fill": nbytes,
             "unfused": {"us_per_fill": round(t_unfused * 1e6, 2), "launches_per_fill": ntags,
                         "fused_speedup": round(t_unfused / t, 2)},
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
-                         "peak_source": src, "traffic": roofline_traffic("copy_tags_f64", "fill")}}
+                         "peak_source": src, "traffic": roofline_traffic("copy_tags_f64", "fill")},
+            "clocks": clocks}
+
+
+def run_fill(args):
+    sub = sub_fill(args, reps=args.steps * 10)
+    line = {"metric": "FillBoundary time per fill (256^3, 64 boxes, 4 comps, 2 ghosts, periodic)",
+            "value": sub["us_per_fill"], "unit": "us", "n_gpus": 1, "steps": args.steps * 10,
+            "warmup": 3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": "fill"}}
+    line.update(sub)
+    print(json.dumps(line), flush=True)
+
+
+# The paper's own triad timings (Sec. 3.2, one MI250X GCD), for context only
+PAPER_TRIAD = {"512x32^3": {"per_box_s": 1.16e-3, "fused_s": 3.67e-4},
+               "1x256^3": {"per_box_s": 3.28e-4, "fused_s": 3.35e-4}}
+
+
+def sub_triad(args, reps=50):
+    """STREAM triad a = b + s c (FP64) over a 256^3 domain as 512 boxes of 32^3 and as one
+    box of 256^3 (the paper's Sec. 3.2 cases): one launch per box against one launch over
+    all boxes, CUDA events on the launching stream; 24 B per cell (fields > L2)."""
+    import torch
+    from paper_2403_12179_gb300 import mg
+    peaks, src = load_peaks()
+    hbm = peaks["hbm_gbs"]
+    ctx = mg.mg_init(0)
+    stream = torch.cuda.Stream()
+    out = {}
+    clk = Clocks(torch.cuda.current_device())
+    for name, box in (("512x32^3", 32), ("1x256^3", 256)):
+        ba = mg.mg_box_array_create(ctx, (0, 0, 0), (255,) * 3, (box,) * 3)
+        a, b, c = (mg.mg_fab_alloc(ctx, ba, 1, 1) for _ in range(3))
+        mg.mg_fab_set_val(ctx, b, 1.0, False, stream)
+        mg.mg_fab_set_val(ctx, c, 2.0, False, stream)
+        cells = 256 ** 3
+        res = {}
+        for form, per_box in (("fused", False), ("per_box", True)):
+            for _ in range(3):
+                mg.mg_triad(ctx, a, b, c, 0.5, per_box, stream)
+            t = _time(stream, lambda k: mg.mg_triad(ctx, a, b, c, 0.5, per_box, stream),
+                      reps if not per_box else max(5, reps // 5))
+            res[form] = {"us": round(t * 1e6, 2), "gbs": round(24 * cells / t / 1e9, 1),
+                         "hbm_frac": round(24 * cells / t / 1e9 / hbm, 4)}
+        res["launches_per_box_form"] = (256 // box) ** 3
+        res["fused_speedup"] = round(res["per_box"]["us"] / res["fused"]["us"], 3)
+        res["paper_mi250x_context"] = PAPER_TRIAD[name]
+        out[name] = res
+        for f in (a, b, c):
+            mg.mg_fab_free(ctx, f, stream)
+    out["clocks"] = clk.stop()
+    out["peak_source"] = src
     mg.mg_finalize(ctx)
+    return out
+
+
+def run_triad(args):
+    sub = sub_triad(args)
+    line = {"metric": "STREAM triad over 512 boxes of 32^3: one launch vs one launch per box",
+            "value": sub["512x32^3"]["fused"]["us"], "unit": "us", "n_gpus": 1, "steps": 50,
+            "warmup": 3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": "triad"}}
+    line.update(sub)
     print(json.dumps(line), flush=True)
 
 
@@ -885,7 +1243,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dirichlet256",
-                    choices=sorted(WORKLOADS) + ["batched512", "serving", "fill"])
+                    choices=sorted(WORKLOADS) + ["batched512", "serving", "fill", "triad"])
+    ap.add_argument("--headline-only", action="store_true",
+                    help="the dirichlet256 line without the other workloads' sub-objects")
     ap.add_argument("--count", type=int, default=512, help="problems in batched512")
     ap.add_argument("--requests", type=int, default=5000, help="requests in serving")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -900,6 +1260,8 @@ def main():
         run_serving(args)
     elif args.workload == "fill":
         run_fill(args)
+    elif args.workload == "triad":
+        run_triad(args)
     elif args.kernels_only:
         run_kernels_only(args, args.workload)
     elif args.impl == "reference":
