@@ -47,6 +47,11 @@ WORKLOADS = {
     "periodic64": dict(n=64, box=32, periodic=(1, 1, 1), precision="f64",
                        desc="64^3 periodic, 8 boxes of 32^3, rhs = -12 pi^2 prod sin(2 pi x) + "
                             "U(-1e-3,1e-3) seed 1, mean removed, V(2,2), tol 1e-10"),
+    "mixed256": dict(n=256, box=64, periodic=(0, 0, 0), precision="mixed",
+                     desc="256^3 homogeneous Dirichlet, 64 boxes of 64^3, rhs = N(0,1) seed 2 "
+                          "smoothed by one damped-Jacobi pass, FP32 inner V(2,2) / FP64 outer "
+                          "residual, correction and bottom, tol 1e-10 (a smaller mixed case, for "
+                          "profiling)"),
     "mixed512": dict(n=512, box=128, periodic=(0, 0, 0), precision="mixed",
                      desc="512^3 homogeneous Dirichlet, 64 boxes of 128^3, 16 Gaussian blobs + "
                           "N(0,1e-3) seed 5, FP32 inner V(2,2) / FP64 outer residual, correction "
@@ -67,7 +72,7 @@ def load_peaks():
 def make_rhs(wl):
     from paper_2403_12179_gb300 import inputs
     n = wl["n"]
-    if wl is WORKLOADS["dirichlet256"]:
+    if wl is WORKLOADS["dirichlet256"] or wl is WORKLOADS["mixed256"]:
         return inputs.dirichlet_jacobi(n, seed=2)
     if wl is WORKLOADS["periodic64"]:
         return inputs.periodic_sine(n, seed=1)

@@ -238,7 +238,9 @@ int mg_fill_boundary_unfused(mg_ctx_t ctx, mg_fab_t fab, const mg_bc* bc, void* 
  *   phi's ghosts as they are (fill them first); rhs needs no ghosts.
  * color 0 / 1 | MG_SMOOTH_DIRECT_READS: the same half-sweep reading each box's neighbours
  *   (periodic images; the negated boundary cell across a Dirichlet face) directly instead of
- *   ghost cells, as the solver does; boxes must form a regular grid (else MG_EINVAL).
+ *   ghost cells, as the solver does; boxes must form a regular grid and periodic extents
+ *   must be even (else MG_EINVAL: an odd periodic extent makes a cell's periodic image one of
+ *   its own colour).
  * color 2: one full sweep, equal to fill, red, fill, black; with phi nghost >= 2 and rhs
  *   nghost >= 1 it runs as one fused kernel after one fill of each.
  * Update: phi_c = (s - h^2 rhs_c) / 6, s = x- + x+ + y- + y+ + z- + z+ (in that order). */
@@ -358,10 +360,18 @@ int mg_submit(mg_ctx_t ctx, mg_fab_t rhs, mg_fab_t phi, const mg_bc* bc, double 
  * untouched until mg_poll reports completion.  With phi_is_guess = 0, phi may be the rhs
  * array itself (rhs is copied in before phi is written).  Otherwise as mg_submit: FP64 or mixed
  * precision per opt, results bit-identical to mg_solve on the same data.
+ * When a host-memory request completes, its workspace (fine-level fabs and level hierarchy)
+ * stays resident for the next request of the same shape (box array, faces and options),
+ * which is then admitted without any planning; idle workspaces are released, oldest first,
+ * when the pool needs room for another request, and all at once by mg_server_trim.
  * Errors: MG_EINVAL (bad domain, box size or options), MG_EAGAIN (queue full). */
 int mg_submit_host(mg_ctx_t ctx, const int dom_lo[3], const int dom_hi[3], const int max_box[3],
                    const mg_bc* bc, const double* rhs, double* phi, int phi_is_guess, double tol,
                    const mg_options* opt, mg_ticket_t* out);
+
+/* Release the scheduler's idle host-memory workspaces (see mg_submit_host) in stream order;
+ * returns once they are gone.  Workspaces in use are not touched. */
+int mg_server_trim(mg_ctx_t ctx);
 
 /* Serving statistics since the scheduler started (no counterpart in the paper). */
 typedef struct {

@@ -47,9 +47,10 @@ struct Member {
   mg_result res{};
   int64_t ticket = 0;
   double t_submit = -1.0;  // served solves: submission time
-  // host-memory requests: the fabs and box array the scheduler made for this solve, and
-  // where its answer goes
+  // host-memory requests: the workspace (box array, fine-level fabs, hierarchy) the
+  // scheduler lent this solve, and where its answer goes
   int64_t own_ba = 0, own_rhs = 0, own_phi = 0;
+  std::string ws_key;
   double* phi_host = nullptr;
 };
 
@@ -487,10 +488,21 @@ struct Ctx::Server {
     // host-memory requests (mg_submit_host): rhs == phi == 0, the box array chopped at
     // submission, the fabs allocated from the pool at admission
     std::shared_ptr<BoxArrayObj> hba;
+    std::string ws_key;  // requests with equal keys can share a workspace, one at a time
     const double* rhs_host = nullptr;
     double* phi_host = nullptr;
     int phi_is_guess = 0;
   };
+  // Workspaces of retired host-memory requests, kept for the next request of the same shape
+  // (box array, faces, options) -- its hierarchy stays resident, so admitting it costs two
+  // copies and no planning.  Oldest first; released, oldest first, when the pool needs room,
+  // and all at once by mg_server_trim.
+  struct Workspace {
+    std::string key;
+    int64_t ba = 0, rhs = 0, phi = 0;
+  };
+  std::deque<Workspace> idle;
+  bool trim = false;  // mg_server_trim waiting
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Req> queue;
@@ -511,15 +523,46 @@ struct Ctx::Server {
 
 namespace {
 
-// Releases, in stream order, what the scheduler made for a host-memory request.
-void release_own(Ctx& c, Member& m, cudaStream_t s) {
-  if (m.own_phi) release_fab(c, m.own_phi, s);
-  if (m.own_rhs) release_fab(c, m.own_rhs, s);
-  if (m.own_ba) {
-    std::lock_guard<std::mutex> lk(c.mu);
-    c.bas.erase(m.own_ba);
+// Releases, in stream order, a host-memory workspace: its hierarchy, fabs and box array.
+void release_ws(Ctx& c, int64_t ba, int64_t rhs, int64_t phi, cudaStream_t s) {
+  if (rhs || phi) {
+    std::lock_guard<std::recursive_mutex> hl(c.hier_mu);
+    std::vector<std::shared_ptr<Hierarchy>> rest;
+    for (auto& h : c.hier)
+      if (!(h->rhs_id == rhs && h->phi_id == phi)) rest.push_back(h);
+    c.hier.swap(rest);
   }
+  if (phi) release_fab(c, phi, s);
+  if (rhs) release_fab(c, rhs, s);
+  if (ba) {
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.bas.erase(ba);
+  }
+}
+void release_own(Ctx& c, Member& m, cudaStream_t s) {
+  release_ws(c, m.own_ba, m.own_rhs, m.own_phi, s);
   m.own_ba = m.own_rhs = m.own_phi = 0;
+}
+// Releases the oldest idle workspace; false if there is none.
+bool evict_idle(Ctx& c, Ctx::Server& S, cudaStream_t s) {
+  if (S.idle.empty()) return false;
+  const auto w = S.idle.front();
+  S.idle.pop_front();
+  release_ws(c, w.ba, w.rhs, w.phi, s);
+  return true;
+}
+// Takes the most recently idle workspace with this key into m; false if there is none.
+bool take_idle(Ctx::Server& S, const std::string& key, Member& m) {
+  for (size_t i = S.idle.size(); i-- > 0;)
+    if (S.idle[i].key == key) {
+      m.own_ba = S.idle[i].ba;
+      m.own_rhs = S.idle[i].rhs;
+      m.own_phi = S.idle[i].phi;
+      m.ws_key = key;
+      S.idle.erase(S.idle.begin() + (long)i);
+      return true;
+    }
+  return false;
 }
 
 void server_loop(Ctx* c) {
@@ -535,7 +578,14 @@ void server_loop(Ctx* c) {
     {
       std::unique_lock<std::mutex> lk(S.mu);
       if (active.empty())
-        S.cv_work.wait(lk, [&] { return S.stop || !S.queue.empty(); });
+        S.cv_work.wait(lk, [&] { return S.stop || S.trim || !S.queue.empty(); });
+      if (S.trim) {
+        while (evict_idle(*c, S, s)) {
+        }
+        cudaStreamSynchronize(s);
+        S.trim = false;
+        S.cv_done.notify_all();
+      }
       if (S.stop && S.queue.empty() && active.empty()) break;
       // admission: while a slot is free (pool room is checked when the hierarchy is built)
       while (!S.queue.empty() && (int)(active.size() + admit.size()) < S.max_active) {
@@ -557,13 +607,34 @@ void server_loop(Ctx* c) {
         int64_t rid = r.rhs, pid = r.phi;
         if (r.hba) {
           // the request's fine level comes from the pool too: rhs (1 ghost layer) and phi
-          // (2, so that the fused smoother may run on it), filled from host memory
-          m->own_ba = c->add_ba(r.hba);
-          m->own_rhs = rid = add_pool_fab(*c, r.hba, m->own_ba, 1, 1, DT_F64, s);
-          m->own_phi = pid = add_pool_fab(*c, r.hba, m->own_ba, 1, 2, DT_F64, s);
+          // (2, so that the fused smoother may run on it), filled from host memory -- in an
+          // idle workspace of the same shape if there is one, else in a new one (made room
+          // for by releasing idle workspaces of other shapes, oldest first)
           m->phi_host = r.phi_host;
+          if (!take_idle(S, r.ws_key, *m)) {
+            for (;;) {
+              try {
+                m->ws_key = r.ws_key;
+                m->own_ba = c->add_ba(r.hba);
+                m->own_rhs = add_pool_fab(*c, r.hba, m->own_ba, 1, 1, DT_F64, s);
+                m->own_phi = add_pool_fab(*c, r.hba, m->own_ba, 1, 2, DT_F64, s);
+                auto fr = c->get_fab(m->own_rhs);
+                auto fp = c->get_fab(m->own_phi);
+                std::lock_guard<std::recursive_mutex> hl(c->hier_mu);
+                get_hierarchy(*c, *fr, *fp, &r.bc, r.p);
+                break;
+              } catch (const MgError& e) {
+                release_own(*c, *m, s);
+                if (e.code != MG_ENOMEM || !evict_idle(*c, S, s)) throw;
+              }
+            }
+          }
+          rid = m->own_rhs;
+          pid = m->own_phi;
           dense_upload(*c, *c->get_fab(rid), r.rhs_host, s);
-          if (r.phi_is_guess) dense_upload(*c, *c->get_fab(pid), r.phi_host, s);
+          auto fp = c->get_fab(pid);
+          if (r.phi_is_guess) dense_upload(*c, *fp, r.phi_host, s);
+          else MG_CK(cudaMemsetAsync(fp->base, 0, fp->bytes, s));
         }
         auto fr = c->get_fab(rid);
         auto fp = c->get_fab(pid);
@@ -641,8 +712,9 @@ void server_loop(Ctx* c) {
       free_slots.push_back(m->slot);
       const int64_t rid = m->H ? m->H->rhs_id : 0, pid = m->H ? m->H->phi_id : 0;
       m->H.reset();
-      // release the solve's hierarchy (coarse levels, tables) in stream order
-      {
+      // release the solve's hierarchy (coarse levels, tables) in stream order; a
+      // host-memory request's workspace is kept whole for the next request of its shape
+      if (!m->own_phi) {
         std::lock_guard<std::recursive_mutex> hl(c->hier_mu);
         std::vector<std::shared_ptr<Hierarchy>> rest;
         for (auto& h : c->hier)
@@ -672,7 +744,12 @@ void server_loop(Ctx* c) {
         if (m->own_phi) {
           m->res.t_end = c->now();
           m->res.seconds = m->res.t_end - m->res.t_start;
-          release_own(*c, *m, s);
+          if (m->res.status == MG_OK || m->res.status == MG_NOT_CONVERGED) {
+            S.idle.push_back({m->ws_key, m->own_ba, m->own_rhs, m->own_phi});
+            m->own_ba = m->own_rhs = m->own_phi = 0;
+          } else {
+            release_own(*c, *m, s);
+          }
         }
     }
     for (auto& m : leaving) {
@@ -686,6 +763,8 @@ void server_loop(Ctx* c) {
       std::lock_guard<std::mutex> lk(S.mu);
       S.stats.retire_seconds += secs_since(t_ret0);
     }
+  }
+  while (evict_idle(*c, S, s)) {
   }
   if (st.dev) st.dev->reset(s);
   for (NormBuf& nb : S.norms) nb.release(s);
@@ -735,6 +814,18 @@ int server_submit_host(Ctx& c, std::shared_ptr<BoxArrayObj> ba, const double* rh
   std::lock_guard<std::mutex> lk(S.mu);
   if (S.queue.size() >= S.max_queue) fail(MG_EAGAIN, "serving queue full");
   Ctx::Server::Req r{S.next_ticket++, 0, 0, *bc, tol, p, c.now()};
+  {
+    // workspace key: the boxes, the faces and every option the hierarchy depends on
+    std::string& k = r.ws_key;
+    auto put = [&](const void* d, size_t n) { k.append((const char*)d, n); };
+    put(&ba->ba.dom, sizeof(Box));
+    for (const Box& b : ba->ba.boxes) put(&b, sizeof(Box));
+    put(bc, sizeof(mg_bc));
+    const int ip[8] = {p.nu1, p.nu2, p.precision, p.smoother, p.coarse_cells, p.direct_reads,
+                       p.prolong, 0};
+    put(ip, sizeof ip);
+    put(&p.h, sizeof p.h);
+  }
   r.hba = std::move(ba);
   r.rhs_host = rhs;
   r.phi_host = phi;
@@ -769,6 +860,15 @@ void server_stats(Ctx& c, mg_server_stats* out) {
   }
   std::lock_guard<std::mutex> lk(c.server->mu);
   *out = c.server->stats;
+}
+
+void server_trim(Ctx& c) {
+  if (!c.server) return;
+  Ctx::Server& S = *c.server;
+  std::unique_lock<std::mutex> lk(S.mu);
+  S.trim = true;
+  S.cv_work.notify_all();
+  S.cv_done.wait(lk, [&] { return !S.trim; });
 }
 
 void server_stop(Ctx& c) {

@@ -330,17 +330,22 @@ __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
 // par + 2l + 4Gk + 2G together.
 // DIRECT: box-face neighbours through DRow::nbd / nbf (rows without that information read
 // their ghost cells); else ghost cells, through plain offsets.
-// norms != null (single-segment launches, DIRECT only): also the max-norm of the residual of
-// every updated cell just after its update, into norms[slot + solve].  The neighbour sum of
-// the update serves, since the other colour's cells are unchanged by this half-sweep --
-// except where a read is the cell's own value negated (a Dirichlet face): those cells sum
-// again, reading their new value.  (With an odd periodic extent an image could be the cell's
-// own colour; callers use this on even periodic extents only.)
-// Resident blocks per SM the half-sweep is built for (register budget): the norm variant
-// holds more live values.
+// MODE 1 (norms != null, single-segment launches, DIRECT only): also the max-norm of the
+// residual of every updated cell just after its update, into norms[slot + solve].  The
+// neighbour sum of the update serves, since the other colour's cells are unchanged by this
+// half-sweep -- except where a read is the cell's own value negated (a Dirichlet face):
+// those cells sum again, reading their new value.  (With an odd periodic extent an image
+// could be the cell's own colour; callers use this on even periodic extents only.)
+// MODE 2 (same conditions): the max-norm of the residual of every updated cell just BEFORE
+// its update -- the neighbour sum of the update is exactly the one that residual needs,
+// Dirichlet reads included, since they read the cell's value before the update -- and the
+// value before the update saved to v[2] (same layout as phi), so that the half-sweep can be
+// undone (k_restore_colour).
+// Resident blocks per SM the half-sweep is built for (register budget): the norm variants
+// hold more live values.
 constexpr int kSweepMinBlocks = 4, kNormMinBlocks = 4;
-template <class T, bool DIRECT, bool NORM, int G>
-__global__ void __launch_bounds__(kThreads, NORM ? kNormMinBlocks : kSweepMinBlocks)
+template <class T, bool DIRECT, int MODE, int G>
+__global__ void __launch_bounds__(kThreads, MODE ? kNormMinBlocks : kSweepMinBlocks)
     k_rbgs_half(SegList L, long long nrows, long long per, int color, unsigned long long* norms) {
   // A lane updates cells x and x + 2G of a pair step together (both of this colour: their
   // neighbours are of the other colour and unchanged, so both loads go first -- two
@@ -353,6 +358,7 @@ __global__ void __launch_bounds__(kThreads, NORM ? kNormMinBlocks : kSweepMinBlo
     const int y = (int)lr % n1, z = (int)lr / n1;
     T* phi = line<T>(R.v[0], y, z);
     const T* rhs = line<T>(R.v[1], y, z);
+    T* save = MODE == 2 ? line<T>(R.v[2], y, z) : nullptr;
     const T h2 = level_const<T>(R.h2), ih2 = level_const<T>(R.ih2);
     const int par = (color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1;
     cur = slot + R.solve;
@@ -368,13 +374,26 @@ __global__ void __launch_bounds__(kThreads, NORM ? kNormMinBlocks : kSweepMinBlo
         const T s2 = two ? sum(x2) : T(0);
         const T r1 = rhs[x];
         const T r2 = two ? rhs[x2] : T(0);
+        T o1 = T(0), o2 = T(0);
+        if (MODE == 2) {
+          o1 = phi[x];
+          o2 = two ? phi[x2] : T(0);
+        }
         const T u1 = gs_update(s1, r1, h2);
+        if (MODE == 2) {
+          norm(s1, o1, r1);
+          save[x] = o1;
+        }
         phi[x] = u1;
-        if (NORM) norm(resum(x, s1), u1, r1);
+        if (MODE == 1) norm(resum(x, s1), u1, r1);
         if (two) {
           const T u2 = gs_update(s2, r2, h2);
+          if (MODE == 2) {
+            norm(s2, o2, r2);
+            save[x2] = o2;
+          }
           phi[x2] = u2;
-          if (NORM) norm(resum(x2, s2), u2, r2);
+          if (MODE == 1) norm(resum(x2, s2), u2, r2);
         }
       }
     };
@@ -393,7 +412,23 @@ __global__ void __launch_bounds__(kThreads, NORM ? kNormMinBlocks : kSweepMinBlo
       sweep([&](int x) { return nbr_sum(phi + x, pitch, plane); }, [](int, T s) { return s; });
     }
   });
-  if (NORM) flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
+  if (MODE) flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
+}
+
+// Undo of a MODE 2 half-sweep: cells of colour `color` take back their saved values
+// (v[0] = phi, v[2] = the saved values).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_restore_colour(SegList L, long long nrows, long long per,
+                                                             int color) {
+  const int lane = threadIdx.x & 31;
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)lr % n1, z = (int)lr / n1;
+    T* phi = line<T>(R.v[0], y, z);
+    const T* save = line<T>(R.v[2], y, z);
+    const int par = (color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1;
+    for (int x = par + 2 * lane; x < n0; x += 64) phi[x] = save[x];
+  });
 }
 
 // Residual r = rhs - (s - 6 phi) / h^2, optionally stored, with a fused max-norm into
@@ -857,28 +892,34 @@ int group_lanes(int width, int cells, int lo, int hi) {
 template <class T, bool DIRECT>
 void rbgs_half_g(int G, const Grid& g, cudaStream_t s, const SegList& L, long long nrows, int color,
                  unsigned long long* norms) {
-  if (G == 16) k_rbgs_half<T, DIRECT, false, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
-  else if (G == 8) k_rbgs_half<T, DIRECT, false, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
-  else k_rbgs_half<T, DIRECT, false, 4><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+  if (G == 16) k_rbgs_half<T, DIRECT, 0, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+  else if (G == 8) k_rbgs_half<T, DIRECT, 0, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+  else k_rbgs_half<T, DIRECT, 0, 4><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
 }
-template <class T>
+template <class T, int MODE>
 void rbgs_half_norm_g(int G, const Grid& g, cudaStream_t s, const SegList& L, long long nrows, int color,
                       unsigned long long* norms) {
-  if (G == 16) k_rbgs_half<T, true, true, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
-  else k_rbgs_half<T, true, true, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+  if (G == 16) k_rbgs_half<T, true, MODE, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+  else k_rbgs_half<T, true, MODE, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
 }
 }  // namespace
 
 cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int color, cudaStream_t s,
-                               bool direct, unsigned long long* norms) {
+                               bool direct, unsigned long long* norms, bool pre) {
   if (nrows <= 0) return cudaSuccess;
   if (norms && (L.n != 1 || !direct)) return cudaErrorInvalidValue;
+  if (pre && !norms) return cudaErrorInvalidValue;
   // a line of w cells holds w / 2 of one colour; two per lane
   const int G = group_lanes(L.width, 4, norms ? 8 : 4, 16);
   const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
   if (norms) {
-    if (dt == DT_F64) rbgs_half_norm_g<double>(G, g, s, L, nrows, color, norms);
-    else rbgs_half_norm_g<float>(G, g, s, L, nrows, color, norms);
+    if (dt == DT_F64) {
+      if (pre) rbgs_half_norm_g<double, 2>(G, g, s, L, nrows, color, norms);
+      else rbgs_half_norm_g<double, 1>(G, g, s, L, nrows, color, norms);
+    } else {
+      if (pre) rbgs_half_norm_g<float, 2>(G, g, s, L, nrows, color, norms);
+      else rbgs_half_norm_g<float, 1>(G, g, s, L, nrows, color, norms);
+    }
   } else if (dt == DT_F64) {
     if (direct) rbgs_half_g<double, true>(G, g, s, L, nrows, color, norms);
     else rbgs_half_g<double, false>(G, g, s, L, nrows, color, norms);
@@ -1029,8 +1070,18 @@ cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsign
 // ---- single-table launchers (one segment) ------------------------------------------------
 
 cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
-                             cudaStream_t s, bool direct, unsigned long long* norms, int width) {
-  return launch_rbgs_half_l(dt, one_seg(rows, nbox, 0, width), nrows, color, s, direct, norms);
+                             cudaStream_t s, bool direct, unsigned long long* norms, int width,
+                             bool pre) {
+  return launch_rbgs_half_l(dt, one_seg(rows, nbox, 0, width), nrows, color, s, direct, norms, pre);
+}
+
+cudaError_t launch_restore_colour(int dt, const DRow* rows, int nbox, long long nrows, int color,
+                                  cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  GB_DISPATCH(dt, k_restore_colour, g.blocks, kThreads, 0, s, one_seg(rows, nbox), nrows, g.per, color);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,

@@ -182,9 +182,15 @@ cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int n
 // of |residual| of every updated cell after its update into norms[solve] (valid when the
 // box array's periodic extents are even).  width: the widest box x-extent of the table
 // (0 = unknown; any value gives the same results, it only picks the lanes per row).
+// pre = true (needs norms): the norm is that of each updated cell's residual just before its
+// update, and the values before the update are saved to v[2] (same layout as v[0]) so that
+// launch_restore_colour can undo the half-sweep.
 cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
                              cudaStream_t s, bool direct = false,
-                             unsigned long long* norms = nullptr, int width = 0);
+                             unsigned long long* norms = nullptr, int width = 0, bool pre = false);
+// v[0] = phi, v[2] = saved values: cells of colour `color` take their saved values back.
+cudaError_t launch_restore_colour(int dt, const DRow* rows, int nbox, long long nrows, int color,
+                                  cudaStream_t s);
 
 // v[0] = phi, v[1] = rhs, v[2] = r (p == null: not stored).  norms[solve] receives
 // atomicMax of the bit pattern of |r| (NaN propagates as the largest pattern).  color < 0:
@@ -261,7 +267,8 @@ cudaError_t launch_correct_add(const DRow* rows, int nbox, long long nrows,
 // the totals over all segments.
 cudaError_t launch_copy_tags_l(int dt, const TagList& L, long long nchunks, int ncomp, cudaStream_t s);
 cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int color, cudaStream_t s,
-                               bool direct = false, unsigned long long* norms = nullptr);
+                               bool direct = false, unsigned long long* norms = nullptr,
+                               bool pre = false);
 cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
                               cudaStream_t s, bool direct = false, int color = -1);
 cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s,

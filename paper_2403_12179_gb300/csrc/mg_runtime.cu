@@ -281,6 +281,10 @@ FaceReads direct_neighbours(const FabObj& f, const int periodic[3]) {
   const FabLayout& lay = f.lay;
   const size_t nb = ba.boxes.size();
   if (nb == 0 || lay.g < 1) return out;
+  // an odd periodic extent makes a boundary cell's periodic neighbour a cell of its own
+  // colour, which a half-sweep may be updating at the same time: read filled ghosts there
+  for (int d = 0; d < 3; ++d)
+    if (periodic[d] && (ba.dom.len(d) & 1)) return out;
   int E[3];
   for (int d = 0; d < 3; ++d) E[d] = ba.boxes[0].len(d);
   std::map<std::array<int, 3>, int> at_lo;
@@ -1140,7 +1144,8 @@ int mg_smooth(mg_ctx_t h, mg_fab_t phi, mg_fab_t rhs, const mg_bc* bc, double hh
         const std::string op = "smooth_direct" + std::to_string(code);
         const OpTable& t = op_table(*c, op.c_str(), {phi, rhs}, hv, [&] {
           FaceReads faces = direct_neighbours(*fp, per);
-          if (!faces.ok()) fail(MG_EINVAL, "direct reads need boxes on a regular grid");
+          if (!faces.ok())
+            fail(MG_EINVAL, "direct reads need boxes on a regular grid and even periodic extents");
           OpTable tt = make_table(*c, fp->ba->ba, 0, hv, 0, [&](int b, DRow& R) {
             R.v[0] = fp->view(b);
             R.v[1] = fr->view(b);

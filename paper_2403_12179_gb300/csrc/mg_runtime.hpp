@@ -125,7 +125,9 @@ struct FabObj {
 
 // Face reads of the stencil kernels (DRow::nbd / nbf) for the boxes of fab f under the given
 // BCs.  Returns false, leaving `out` empty, unless the boxes form a regular grid (equal
-// extents on a lattice anchored at the domain's low corner) with one layout, so that each
+// extents on a lattice anchored at the domain's low corner) with one layout and every
+// periodic extent is even (an odd one would make a cell's periodic image one of its own
+// colour, updated by the same half-sweep), so that each
 // face's first ghost layer is exactly one face layer of one box (or its periodic image), or
 // lies across a Dirichlet face; the kernels must then read filled ghost cells.
 struct FaceReads {
@@ -334,6 +336,7 @@ int server_submit_host(Ctx& c, std::shared_ptr<BoxArrayObj> ba, const double* rh
                        int64_t* ticket);
 int server_poll(Ctx& c, int64_t ticket, int timeout_ms, mg_result* res);
 void server_stop(Ctx& c);
+void server_trim(Ctx& c);
 void server_stats(Ctx& c, mg_server_stats* out);
 
 // Bottom matrix (transposed), cached per (n, periodic, h).

@@ -299,6 +299,31 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
   }
   if (H->mixed) H->r0 = internal_fab(c, phi.ba, 0, DT_F64);
   build_tables(c, *H, s);
+  {
+    // speculative red half-sweep with the norm check (see Hierarchy::save0): FP64, the
+    // finest level smoothed by half-sweeps of its own (not inside the coarse-cycle kernel)
+    // that read neighbours directly, pre- and post-smoothing present, even periodic extents
+    // (an odd one maps a cell onto its own colour)
+    int per[3];
+    bc_code(bc, per);
+    bool ok = !H->mixed && H->lc > 0 && p.nu1 >= 1 && p.nu2 >= 1 && !H->L[0].fused &&
+              H->L[0].direct && H->direct0;
+    for (int d = 0; d < 3; ++d)
+      if (per[d] && (lev[0].dom.len(d) & 1)) ok = false;
+    if (ok) {
+      LevelData& D = H->L[0];
+      H->save0 = internal_fab(c, phi.ba, phi.lay.g, DT_F64);
+      FaceReads fr = direct_neighbours(*D.phi, per);
+      D.smooth.d->reset(s);
+      D.smooth = make_table(c, D.bao->ba, 0, D.h, 0, [&](int b, DRow& R) {
+        R.v[0] = D.phi->view(b);
+        R.v[1] = D.rhs->view(b);
+        R.v[2] = H->save0->view(b);
+        fr.apply(b, R);
+      }, s);
+      D.smooth.direct = true;
+    }
+  }
   H->dnorm = c.alloc(16, s);
   MG_CK(cudaStreamSynchronize(s));
   c.hier.push_back(std::move(H));
@@ -310,7 +335,8 @@ namespace {
 // last_norm != null: the final (black) half-sweep also accumulates the residual max-norm of
 // the cells it updates there (the caller adds the red cells).
 void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s,
-            unsigned long long* last_norm = nullptr, bool time_first = false) {
+            unsigned long long* last_norm = nullptr, bool time_first = false,
+            bool skip_first_red = false) {
   int k = 0;
   if (D.fused) {
     // pairs of fused sweeps: phi -> phi2 -> phi
@@ -323,9 +349,10 @@ void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s,
   }
   for (; k < sweeps; ++k)
     for (int color = 0; color < 2; ++color) {
+      if (skip_first_red && k == 0 && color == 0) continue;  // done by the previous step
       if (!D.direct) launch_fill(c, *D.phi, &H.bc, s, 1);  // the half-sweep reads one layer
       const bool last = k + 1 == sweeps && color == 1;
-      const bool timed = time_first && k == 0 && color == 0;
+      const bool timed = time_first && k == 0 && color == 1;
       // (external records: captured into the step graph as event-record nodes)
       if (timed) MG_CK(cudaEventRecordWithFlags(H.sweep_ev[0], s, cudaEventRecordExternal));
       MG_CK(launch_rbgs_half(H.dt, D.smooth.rows(), D.smooth.nbox, D.smooth.nrows, color, s,
@@ -334,13 +361,14 @@ void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s,
     }
 }
 
-void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s, unsigned long long* norm0 = nullptr) {
+void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s, unsigned long long* norm0 = nullptr,
+                    bool skip_first_red = false) {
   const int nl = (int)H.L.size();
   const int top = H.lc < nl ? H.lc : nl - 1;  // levels below `top` run stage by stage
   for (int l = 0; l < top; ++l) {
     LevelData& D = H.L[l];
     if (D.fused) launch_fill(c, *D.rhs, &H.bc, s, 1);  // rhs ghosts for the redundant ring
-    smooth(c, H, D, H.p.nu1, s, nullptr, l == 0 && H.graph_timed);
+    smooth(c, H, D, H.p.nu1, s, nullptr, l == 0 && H.graph_timed, l == 0 && skip_first_red);
     if (!D.direct) launch_fill(c, *D.phi, &H.bc, s, 1);
     MG_CK(launch_residual_restrict(H.dt, D.rr.rows(), D.rr.nbox, D.rr.nrows, s, D.direct,
                                    D.rr.width));
@@ -362,9 +390,22 @@ void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s, unsigned long long* no
 }
 
 // One outer iteration: the cycle (with the mixed-precision scale / correction around it),
-// then the norm check of the new iterate.
-void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
+// then the norm check of the new iterate.  variant 1 / 2 (speculating solves): the cycle
+// (variant 2: without its first finest-level red half-sweep, which the previous step ran),
+// whose last black half-sweep takes the black cells' residual norm, then the next cycle's
+// first red half-sweep, which takes the red cells' residual norm of the same iterate and
+// saves the red values it replaces.
+void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s, int variant) {
   unsigned long long* dn = (unsigned long long*)H.dnorm->p;
+  if (variant > 0) {
+    LevelData& D0 = H.L[0];
+    MG_CK(cudaMemsetAsync(dn, 0, 8, s));
+    enqueue_vcycle(c, H, s, dn, variant == 2);
+    MG_CK(launch_rbgs_half(DT_F64, D0.smooth.rows(), D0.smooth.nbox, D0.smooth.nrows, 0, s, true,
+                           dn, D0.smooth.width, true));
+    MG_CK(cudaMemcpyAsync(H.hnorm, dn, 16, cudaMemcpyDeviceToHost, s));
+    return;
+  }
   if (H.mixed)  // the FP32 right-hand side from the residual of the last norm check; e = 0
     MG_CK(launch_scale_residual_f32(H.scale0.rows(), H.scale0.nbox, H.scale0.nrows, dn, s,
                                     H.scale0.width));
@@ -391,25 +432,28 @@ void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
   MG_CK(cudaMemcpyAsync(H.hnorm, dn, 16, cudaMemcpyDeviceToHost, s));
 }
 
-void run_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
+void drop_graphs(Hierarchy& H) {
+  for (cudaGraphExec_t& g : H.step_graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+void run_step(Ctx& c, Hierarchy& H, cudaStream_t s, int variant) {
   bool graph = H.p.use_graph && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
   if (c.sweep_timing && !H.sweep_ev[0])
     for (cudaEvent_t& e : H.sweep_ev) MG_CK(cudaEventCreate(&e));
-  if (H.step_graph && H.graph_timed != c.sweep_timing) {  // timing switched: capture again
-    cudaGraphExecDestroy(H.step_graph);
-    H.step_graph = nullptr;
-  }
+  if (H.graph_timed != c.sweep_timing) drop_graphs(H);  // timing switched: capture again
   H.graph_timed = c.sweep_timing;
-  if (graph && H.step_graph && H.graph_stream != s) {
-    cudaGraphExecDestroy(H.step_graph);
-    H.step_graph = nullptr;
-  }
-  if (graph && !H.step_graph) {
+  if (graph && H.graph_stream != s) drop_graphs(H);
+  cudaGraphExec_t& G = H.step_graph[variant];
+  if (graph && !G) {
     cudaGraph_t g = nullptr;
     const long long before = launches_so_far();
     MG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     try {
-      enqueue_step(c, H, s);
+      enqueue_step(c, H, s, variant);
     } catch (...) {
       cudaStreamEndCapture(s, &g);
       if (g) cudaGraphDestroy(g);
@@ -417,18 +461,18 @@ void run_step(Ctx& c, Hierarchy& H, cudaStream_t s) {
       throw;
     }
     MG_CK(cudaStreamEndCapture(s, &g));
-    H.graph_kernels = launches_so_far() - before;  // captured, not executed
-    count_launches(-H.graph_kernels);
-    cudaError_t e = cudaGraphInstantiate(&H.step_graph, g, 0);
+    H.graph_kernels[variant] = launches_so_far() - before;  // captured, not executed
+    count_launches(-H.graph_kernels[variant]);
+    cudaError_t e = cudaGraphInstantiate(&G, g, 0);
     cudaGraphDestroy(g);
     MG_CK(e);
     H.graph_stream = s;
   }
   if (graph) {
-    MG_CK(cudaGraphLaunch(H.step_graph, s));
-    count_launches(H.graph_kernels);
+    MG_CK(cudaGraphLaunch(G, s));
+    count_launches(H.graph_kernels[variant]);
   } else {
-    enqueue_step(c, H, s);
+    enqueue_step(c, H, s, variant);
   }
 }
 
@@ -489,16 +533,27 @@ int solve(Ctx& c, int64_t rhs_id, int64_t phi_id, const mg_bc* bc, double tol,
     MG_CK(cudaStreamSynchronize(s));
     rn = 0.0;
   } else {
+    bool pending = false;  // the next cycle's first red half-sweep has run (speculatively)
     for (;;) {
-      if (std::isnan(rn) || std::isinf(rn)) { status = MG_ENAN; break; }
-      if (p.fixed_vcycles >= 0) {
-        if (it == p.fixed_vcycles) break;
+      bool stop = false;
+      if (std::isnan(rn) || std::isinf(rn)) { status = MG_ENAN; stop = true; }
+      else if (p.fixed_vcycles >= 0) {
+        stop = it == p.fixed_vcycles;
       } else {
-        if (rn <= tol * rhsnorm) break;
-        if (it == p.max_iter) { status = MG_NOT_CONVERGED; break; }
+        if (rn <= tol * rhsnorm) stop = true;
+        else if (it == p.max_iter) { status = MG_NOT_CONVERGED; stop = true; }
       }
-      run_step(c, H, s);
+      if (stop) {
+        if (pending) {  // undo the speculative red half-sweep
+          const OpTable& t = H.L[0].smooth;
+          MG_CK(launch_restore_colour(DT_F64, t.rows(), t.nbox, t.nrows, 0, s));
+          MG_CK(cudaStreamSynchronize(s));
+        }
+        break;
+      }
+      run_step(c, H, s, H.save0 ? (pending ? 2 : 1) : 0);
       MG_CK(cudaStreamSynchronize(s));
+      pending = (bool)H.save0;
       rn = bits_to_double(H.hnorm[0]);
       if (H.graph_timed && H.lc > 0 && !H.L[0].fused) {
         float ms = 0.f;
@@ -589,6 +644,15 @@ int mg_submit_host(mg_ctx_t h, const int dom_lo[3], const int dom_hi[3], const i
     if (!chop(dom, max_box, &b->ba, &err)) fail(MG_EINVAL, err);
     SolveParams p = params_from(opt, b->ba);
     return server_submit_host(*c, std::move(b), rhs, phi, phi_is_guess, bc, tol, p, out);
+  });
+}
+
+int mg_server_trim(mg_ctx_t h) {
+  return guard([&] {
+    Ctx* c = (Ctx*)h;
+    if (!c) fail(MG_EINVAL, "ctx is NULL");
+    server_trim(*c);
+    return MG_OK;
   });
 }
 

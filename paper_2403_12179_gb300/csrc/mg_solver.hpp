@@ -42,13 +42,23 @@ struct Hierarchy {
   DevBufP dnorm;  // [0] residual norm bits, [1] rhs norm bits
   unsigned long long* hnorm = nullptr;
   BottomJob job_host{};
-  cudaGraphExec_t step_graph = nullptr;
+  // FP64 solves whose finest level starts each V-cycle with a red half-sweep: that
+  // half-sweep of the next cycle also takes the red cells' residual norm of the current
+  // iterate (it computes the same neighbour sums), replacing a separate residual pass; it
+  // runs speculatively at the end of each step, saving the red values it replaces in save0
+  // (null when the solve does not speculate), and is undone if the stop test ends the solve.
+  std::shared_ptr<FabObj> save0;
+  // step graphs: [0] plain step, [1] first step of a speculating solve (a whole V-cycle,
+  // then the next one's red half-sweep), [2] later steps (the V-cycle without that red
+  // half-sweep, then the next one's)
+  cudaGraphExec_t step_graph[3] = {nullptr, nullptr, nullptr};
+  long long graph_kernels[3] = {0, 0, 0};
   cudaStream_t graph_stream = nullptr;
-  long long graph_kernels = 0;
-  bool graph_timed = false;                  // the step graph records sweep_ev
+  bool graph_timed = false;                  // the step graphs record sweep_ev
   cudaEvent_t sweep_ev[2] = {nullptr, nullptr};
   ~Hierarchy() {
-    if (step_graph) cudaGraphExecDestroy(step_graph);
+    for (cudaGraphExec_t g : step_graph)
+      if (g) cudaGraphExecDestroy(g);
     if (hnorm) cudaFreeHost(hnorm);
     for (cudaEvent_t e : sweep_ev)
       if (e) cudaEventDestroy(e);

@@ -387,6 +387,11 @@ def mg_submit_host(ctx, dom_lo, dom_hi, max_box, bc, rhs_ptr, phi_ptr, phi_is_gu
     return t.value
 
 
+def mg_server_trim(ctx):
+    """Release the scheduler's idle host-memory workspaces."""
+    _ck(lib().mg_server_trim(ctx))
+
+
 class mg_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
                 ("completed", ctypes.c_int64), ("steps", ctypes.c_int64),

@@ -338,8 +338,15 @@ def test_serving_from_host_equals_alone(precision):
             assert res_a.vcycles == r.vcycles
             assert np.array_equal(ph.numpy(), phi_a)
         assert mg.mg_server_stats_get(ctx)["completed"] == len(specs)
-        torch.cuda.synchronize()
-        time.sleep(0.05)
+        # the workspaces stay resident: the same requests again reuse them (the pool does
+        # not grow, and the answers are the same); mg_server_trim releases them
+        _, held = mg.mg_pool_info(ctx)
+        assert held > pool0
+        _, phis2, res2 = _serve_host(ctx, specs, precision, 600)
+        assert mg.mg_pool_info(ctx)[1] <= held + (1 << 20)
+        for a, b, r in zip(phis, phis2, res2):
+            assert r.status == mg.MG_OK and torch.equal(a, b)
+        mg.mg_server_trim(ctx)
         assert mg.mg_pool_info(ctx)[1] <= pool0 + (1 << 20)   # fine levels released too
     finally:
         mg.mg_finalize(ctx)

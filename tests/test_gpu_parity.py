@@ -738,3 +738,56 @@ def test_mixed_iterates_match_oracle_at_64(gctx, orc):
                                  fixed_vcycles=3, mixed=True)
     assert res.vcycles == vc == 3
     assert np.array_equal(phi, o_phi), np.abs(phi - o_phi).max()
+
+
+# ---- binary32 half-sweeps on wide rows (17 to 128 cells) -------------------------------
+
+ROWS_CASES = [((79, 23, 11), (40, 12, 6)), ((63, 31, 15), (64, 16, 8)),
+              ((99, 19, 9), (100, 10, 5)), ((63, 63, 31), (32, 32, 32)),
+              ((33, 16, 7), (17, 17, 8))]
+
+
+@pytest.mark.parametrize("dom,mb", ROWS_CASES)
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (1, 0, 1)])
+@pytest.mark.parametrize("direct", [False, True])
+def test_rbgs_half_wide_rows_bitwise(gctx, orc, dom, mb, periodic, direct):
+    """Binary32 half-sweeps on rows of 17 to 128 cells (one, two and four lane steps per
+    row, ragged widths), both colours, reading ghost cells or (regular box grids) the
+    neighbouring boxes directly -- with every ghost cell NaN, so a stray ghost read would
+    show -- equal the oracle bit for bit."""
+    h = 1.0 / (dom[0] + 1)
+    ba, boxes = _ba(gctx, dom, mb)
+    regular = all((dom[d] + 1) % mb[d] == 0 for d in range(3))
+    odd_periodic = any(periodic[d] and (dom[d] + 1) % 2 for d in range(3))
+    phi, rhs = _level_inputs(orc, boxes, dom, periodic, 1, 0, 34, np.float32)
+    bc = mg.make_bc(periodic)
+    if direct and (not regular or odd_periodic):
+        # direct reads need a regular box grid and even periodic extents (an odd one would
+        # make a boundary cell's periodic image a cell of its own colour): refused
+        fp, fr = gu.to_fab(gctx, ba, phi, 1, mg.MG_F32), gu.to_fab(gctx, ba, rhs, 0, mg.MG_F32)
+        with pytest.raises(mg.MgError) as e:
+            mg.mg_smooth(gctx, fp, fr, bc, h, mg.MG_SMOOTH_DIRECT_READS)
+        assert e.value.code == mg.MG_EINVAL
+        mg.mg_fab_free(gctx, fp)
+        mg.mg_fab_free(gctx, fr)
+        return
+    src = phi
+    if direct:
+        src = [a.copy() for a in phi]
+        for a in src:
+            v = a[:, 1:-1, 1:-1, 1:-1].copy()
+            a[...] = np.nan
+            a[:, 1:-1, 1:-1, 1:-1] = v
+    fp, fr = gu.to_fab(gctx, ba, src, 1, mg.MG_F32), gu.to_fab(gctx, ba, rhs, 0, mg.MG_F32)
+    ref = phi
+    for color in (0, 1, 0):
+        ref = orc.fill_boundary(Z3, dom, periodic, boxes, ref, 1)
+        ref = orc.rbgs(Z3, dom, boxes, h, ref, 1, rhs, 0, color)
+        if not direct:
+            mg.mg_fill_boundary(gctx, fp, bc)
+        mg.mg_smooth(gctx, fp, fr, bc, h, color | (mg.MG_SMOOTH_DIRECT_READS if direct else 0))
+        got = gu.from_fab(gctx, fp, len(boxes))
+        for a, r in zip(got, ref):
+            assert np.array_equal(gu.valid(a, 1), gu.valid(r, 1))
+    mg.mg_fab_free(gctx, fp)
+    mg.mg_fab_free(gctx, fr)
