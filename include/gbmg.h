@@ -389,6 +389,43 @@ int mg_server_stats_get(mg_ctx_t ctx, mg_server_stats* out);
  * MG_EINVAL for an unknown ticket. */
 int mg_poll(mg_ctx_t ctx, mg_ticket_t ticket, int timeout_ms, mg_result* res);
 
+/* ---- two-level AMR composite solve (Sec. 1, Sec. 2: AMR hierarchy, inter-level ops) ---- */
+
+/* Composite Poisson problem on two levels (refinement ratio 2): level 0 (fabs rhs0 / phi0 on
+ * a box array over the domain [0, n0), any faces from bc) and level 1 (rhs1 / phi1 on a box
+ * array whose domain is a coarse box region [A, B) refined by 2, i.e. fine cells [2A, 2B),
+ * with A >= 1 and B <= n0 - 1 in every dimension and even box bounds).  Unknowns are the fine
+ * cells and the coarse cells outside the region; the paper gives no coarse/fine
+ * discretisation, so the one here is this library's reading:
+ *  - fine cells: the 7-point operator with h1 = h0 / 2; a neighbour across the coarse/fine
+ *    boundary is the ghost value g = 8/15 c + 2/3 f1 - 1/5 f2, where f1, f2 are the first two
+ *    fine cells inside along the normal and c is the quadratic interpolation, over the 3 x 3
+ *    coarse cells of the layer just outside the region, at the ghost's tangential position
+ *    (3-point Lagrange weights at offset -1/4 or +1/4 coarse cells, lower-numbered tangential
+ *    dimension first);
+ *  - uncovered coarse cells: the 7-point operator with h0, except that the flux through a face
+ *    shared with the region is the mean of the four fine fluxes (phi_f - g_f) / h1 through it
+ *    (flux matching: the composite operator is conservative);
+ *  - covered coarse cells are not unknowns; on return they hold the mean of their 8 children.
+ * h0 = opt->h, or 1 / n0[0].  FP64 fabs, 1 component, phi0 and phi1 with >= 1 ghost layer.
+ * The iteration (stop test ||f - A phi||_inf <= tol ||f||_inf before each, over fine and
+ * uncovered coarse cells): one V(nu1, nu2) cycle of the single-level solver on level 0 for the
+ * composite residual (covered cells: the mean of the fine residual), added to phi0 and, by
+ * injection, to phi1; then nu1 + nu2 red-black sweeps on level 1 with the coarse/fine ghosts
+ * refreshed before each colour; then the covered coarse cells take their children's mean.
+ * res->vcycles counts these iterations.  Tables and work fabs are built on first use and
+ * cached per (fabs, bc, options) until one of the fabs is freed.  Returns res->status. */
+int mg_amr2_solve(mg_ctx_t ctx, mg_fab_t rhs0, mg_fab_t phi0, mg_fab_t rhs1, mg_fab_t phi1,
+                  const mg_bc* bc, double tol, const mg_options* opt, mg_result* res);
+
+/* The composite residual of mg_amr2_solve's problem at the current phi (after the covered
+ * coarse cells of phi0 take the mean of their children): r0 (a level-0 fab without ghosts,
+ * covered cells: the mean of the fine residual) and r1 (level 1, no ghosts), either may be 0;
+ * its max-norm over fine and uncovered coarse cells into *norm (if non-NULL).  h <= 0: 1 / n0[0].
+ * Synchronous. */
+int mg_amr2_residual(mg_ctx_t ctx, mg_fab_t rhs0, mg_fab_t phi0, mg_fab_t rhs1, mg_fab_t phi1,
+                     const mg_bc* bc, double h, mg_fab_t r0, mg_fab_t r1, double* norm);
+
 /* ---- calibration (Sec. 3.1-3.2 STREAM triad; FP64 rate) ------------------------------ */
 
 /* STREAM triad a = b + s c (computed as one fma per cell) on the valid cells of three

@@ -146,7 +146,6 @@ def apply(phi0, phi1, g):
     a1 = (pf[1:-1, 1:-1, :-2] + pf[1:-1, 1:-1, 2:] + pf[1:-1, :-2, 1:-1] + pf[1:-1, 2:, 1:-1] +
           pf[:-2, 1:-1, 1:-1] + pf[2:, 1:-1, 1:-1] - 6.0 * c) / (h1 * h1)
     pc = _coarse_padded(phi0, g)
-    cc = pc[1:-1, 1:-1, 1:-1]
     # fluxes through the +x, +y, +z faces of every coarse cell (face i between i and i+1)
     fx = (pc[1:-1, 1:-1, 1:] - pc[1:-1, 1:-1, :-1]) / h0   # (nz, ny, nx + 1)
     fy = (pc[1:-1, 1:, 1:-1] - pc[1:-1, :-1, 1:-1]) / h0
@@ -354,3 +353,48 @@ def sample(g, fn):
     Zc, Yc, Xc = np.meshgrid(xc[2], xc[1], xc[0], indexing="ij")
     Zf, Yf, Xf = np.meshgrid(xf[2], xf[1], xf[0], indexing="ij")
     return fn(Xc, Yc, Zc), fn(Xf, Yf, Zf)
+
+
+# ---- the iteration the GPU solver runs, step by step ----------------------------------
+
+def fine_half_sweep(phi0, phi1, f1, g, color):
+    """One red-black half-sweep of the fine level (colour on fine global indices), the
+    coarse/fine ghosts taken from phi0 and phi1 as they are before it."""
+    pf = cf_ghosts(phi0, phi1, g)
+    n1 = g.n1
+    k, j, i = np.meshgrid(np.arange(n1[2]), np.arange(n1[1]), np.arange(n1[0]), indexing="ij")
+    col = ((i + 2 * g.A[0]) + (j + 2 * g.A[1]) + (k + 2 * g.A[2])) % 2 == color
+    s = (pf[1:-1, 1:-1, :-2] + pf[1:-1, 1:-1, 2:] + pf[1:-1, :-2, 1:-1] + pf[1:-1, 2:, 1:-1] +
+         pf[:-2, 1:-1, 1:-1] + pf[2:, 1:-1, 1:-1])
+    return np.where(col, (s - g.h1 * g.h1 * f1) / 6.0, phi1)
+
+
+def iterate(f0, f1, g, k, nu1=2, nu2=2):
+    """k iterations of the composite scheme from phi = 0: composite residual; one V(nu1, nu2)
+    cycle of the single-level oracle on level 0 for it (covered cells: the mean of the fine
+    residual); phi0 += e0, phi1 += e0 of the parent; nu1 + nu2 fine red-black sweeps;
+    covered coarse cells take the mean of their children.  Returns (phi0, phi1, history of
+    the composite residual norm relative to ||f||)."""
+    import oracle
+    phi0, phi1 = np.zeros(g.n0[::-1]), np.zeros(g.n1[::-1])
+    cov = g.covered()
+    fn = max(float(np.abs(f0[~cov]).max()), float(np.abs(f1).max()))
+    dlo, dhi = (0, 0, 0), tuple(v - 1 for v in g.n0)
+    boxes = oracle.chop(dlo, dhi, g.n0)
+    hist = []
+    for _ in range(k):
+        r0, r1, rn = residual(phi0, phi1, f0, f1, g)
+        hist.append(rn / fn)
+        rc = average_down(r0, r1, g)
+        e0, st, _, _ = oracle.solve(dlo, dhi, g.periodic, boxes, g.h0, rc, fixed_vcycles=1,
+                                    nu1=nu1, nu2=nu2)
+        phi0 = phi0 + e0
+        sub = e0[g.A[2]:g.B[2], g.A[1]:g.B[1], g.A[0]:g.B[0]]
+        phi1 = phi1 + np.repeat(np.repeat(np.repeat(sub, 2, 0), 2, 1), 2, 2)
+        for _s in range(nu1 + nu2):
+            for color in (0, 1):
+                phi1 = fine_half_sweep(phi0, phi1, f1, g, color)
+        phi0 = average_down(phi0, phi1, g)
+    _, _, rn = residual(phi0, phi1, f0, f1, g)
+    hist.append(rn / fn)
+    return phi0, phi1, np.array(hist)

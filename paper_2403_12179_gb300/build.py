@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libgbmg.so")
 OBJ_DIR = os.path.join(HERE, "_build")
 SOURCES = ["mg_host.cpp", "mg_kernels.cu", "mg_fused.cu", "mg_runtime.cu", "mg_solver.cu",
-           "mg_batch.cu", "mg_noalloc.cu", "mg_coarse.cu", "mg_calib.cu"]
+           "mg_batch.cu", "mg_noalloc.cu", "mg_coarse.cu", "mg_calib.cu", "mg_amr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

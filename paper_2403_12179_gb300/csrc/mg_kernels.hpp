@@ -236,6 +236,9 @@ cudaError_t coarse_opt_in(int dt, size_t smem);
 cudaError_t launch_coarse_cycle(int dt, const CoarseJob* jobs, int njobs, size_t smem,
                                 cudaStream_t s);
 
+// v[0] += v[1] on valid cells.
+cudaError_t launch_add_valid(int dt, const DRow* rows, int nbox, long long nrows, cudaStream_t s);
+
 // v[0] = field: valid cells = value.
 cudaError_t launch_set_valid(int dt, const DRow* rows, int nbox, long long nrows, double value,
                              cudaStream_t s);

@@ -757,6 +757,7 @@ int mg_finalize(mg_ctx_t h) {
       server_stop(*c);
       cudaDeviceSynchronize();
     }
+    amr_drop_plans(*c, 0);
     destroy_hierarchies(*c);
     c->op_cache.clear();
     c->fused_cache.clear();
@@ -1005,6 +1006,7 @@ int mg_fab_free(mg_ctx_t h, mg_fab_t fab, void* stream) {
       f = it->second;
       c->fabs.erase(it);
     }
+    amr_drop_plans(*c, fab);
     drop_hierarchies_of(*c, fab);
     drop_cached_ops_of(*c, fab);
     // Order the release after the caller's stream and the context stream.

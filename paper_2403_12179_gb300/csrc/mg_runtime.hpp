@@ -336,6 +336,8 @@ int server_submit_host(Ctx& c, std::shared_ptr<BoxArrayObj> ba, const double* rh
                        int64_t* ticket);
 int server_poll(Ctx& c, int64_t ticket, int timeout_ms, mg_result* res);
 void server_stop(Ctx& c);
+// Two-level AMR plans (mg_amr.cu): drop those using fab `fab` (0: all of the context).
+void amr_drop_plans(Ctx& c, int64_t fab);
 void server_trim(Ctx& c);
 void server_stats(Ctx& c, mg_server_stats* out);
 

@@ -484,6 +484,11 @@ double bits_to_double(unsigned long long b) {
 
 }  // namespace
 
+void enqueue_correction_cycle(Ctx& c, Hierarchy& H, cudaStream_t s) {
+  MG_CK(cudaMemsetAsync(H.phi0->base, 0, H.phi0->bytes, s));
+  enqueue_vcycle(c, H, s);
+}
+
 void drop_hierarchies_of(Ctx& c, int64_t fab_id) {
   std::lock_guard<std::recursive_mutex> lk(c.hier_mu);
   bool any = false;

@@ -69,4 +69,8 @@ struct Hierarchy {
 // Cached per (rhs fab, phi fab, bc, options); builds coarse levels, tables and plans.
 Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, const SolveParams& p);
 
+// One V-cycle for the hierarchy's problem from a zero guess: phi (the caller's level-0 fab,
+// ghosts included) is zeroed, then the cycle is enqueued on s; no norm is taken.
+void enqueue_correction_cycle(Ctx& c, Hierarchy& H, cudaStream_t s);
+
 }  // namespace gbmg

@@ -445,6 +445,26 @@ class BoxView:
                 "strides": self.strides, "version": 3}
 
 
+def mg_amr2_solve(ctx, rhs0, phi0, rhs1, phi1, bc, tol=1e-10, opt=None):
+    """Two-level AMR composite solve (level 1 a refined box region of level 0)."""
+    res = mg_result()
+    rc = lib().mg_amr2_solve(ctx, ctypes.c_int64(rhs0), ctypes.c_int64(phi0), ctypes.c_int64(rhs1),
+                             ctypes.c_int64(phi1), ctypes.byref(bc), ctypes.c_double(tol),
+                             ctypes.byref(opt) if opt is not None else None, ctypes.byref(res))
+    if rc < 0 and rc not in (MG_NOT_CONVERGED, MG_ENAN):
+        _ck(rc)
+    return res
+
+
+def mg_amr2_residual(ctx, rhs0, phi0, rhs1, phi1, bc, h=0.0, r0=0, r1=0):
+    """Composite residual into r0 / r1 (fabs without ghosts, or 0); returns its max-norm."""
+    nrm = ctypes.c_double(0.0)
+    _ck(lib().mg_amr2_residual(ctx, ctypes.c_int64(rhs0), ctypes.c_int64(phi0), ctypes.c_int64(rhs1),
+                               ctypes.c_int64(phi1), ctypes.byref(bc), ctypes.c_double(h),
+                               ctypes.c_int64(r0), ctypes.c_int64(r1), ctypes.byref(nrm)))
+    return nrm.value
+
+
 def mg_triad(ctx, a, b, c, s, per_box=False, stream=None):
     """a = b + s c on valid cells: one launch over all boxes, or one launch per box."""
     _ck(lib().mg_triad(ctx, ctypes.c_int64(a), ctypes.c_int64(b), ctypes.c_int64(c),

@@ -123,3 +123,27 @@ def test_exact_solve_has_zero_residual(periodic):
     assert rn <= 1e-10 * max(np.abs(f0).max(), np.abs(f1).max())
     # covered coarse cells hold the mean of their children
     np.testing.assert_allclose(p0, amr.average_down(p0, p1, g), rtol=0, atol=0)
+
+
+def test_iteration_converges_to_the_exact_composite_solution():
+    """The composite iteration (coarse V-cycle on the composite residual, fine sweeps with
+    coarse/fine ghosts) contracts the residual by at least 4x per step and reaches the sparse
+    direct solution."""
+    g = amr.Geometry((16, 16, 16), (4, 4, 4), (12, 12, 12), (0, 0, 0))
+    f0, f1 = _rand(g, 84)
+    p0, p1, hist = amr.iterate(f0, f1, g, 12)
+    assert np.all(hist[1:] <= 0.25 * hist[:-1]) and hist[-1] < 1e-10
+    e0, e1 = amr.solve(f0, f1, g)
+    cov = g.covered()
+    assert np.abs(p1 - e1).max() <= 1e-10 * np.abs(e1).max()
+    assert np.abs((p0 - e0)[~cov]).max() <= 1e-10 * np.abs(e1).max()
+
+
+def test_composite_inverse_norm_bound_at_8():
+    """||A^-1||_inf of the composite operator (Dirichlet unit cube, refined middle) is below
+    0.1 -- the constant the GPU tests use to turn a residual into an error bound (the
+    continuous problem's value is about 0.056)."""
+    g = amr.Geometry((8, 8, 8), (2, 2, 2), (6, 6, 6), (0, 0, 0))
+    A = amr.assemble(g).toarray()
+    inv = np.linalg.inv(A)
+    assert np.abs(inv).sum(axis=1).max() < 0.1
