@@ -633,6 +633,19 @@ __global__ void __launch_bounds__(256) k_fp64_probe(int iters, double b, double 
   if (s == -1.0) g_probe_sink = s;
 }
 
+// a += b on valid cells: v[0] = a, v[1] = b.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_add_valid(SegList L, long long nrows, long long per) {
+  const int lane = threadIdx.x & 31;
+  for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int y = (int)lr % n1, z = (int)lr / n1;
+    T* a = line<T>(R.v[0], y, z);
+    const T* b = line<T>(R.v[1], y, z);
+    for (int x = lane; x < n0; x += 32) a[x] = Ar<T>::add(a[x], b[x]);
+  });
+}
+
 template <class T>
 __global__ void k_set_flat(T* p, long long n, T value) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -716,7 +729,8 @@ __device__ __forceinline__ double pow2_floor_inv(double s) { return bits::pow2(-
 
 // r32 = float(r * 2^-e) with 2^e <= ||r||_inf < 2^(e+1), from the FP64 residual stored by the
 // preceding norm check (the same values the norm was taken over), and the FP32 correction's
-// initial guess e32 = 0.  G lanes per x-line, four cells per lane step, loads first.
+// initial guess e32 = 0.  G lanes per x-line, kStreamCells cells per lane step, loads first.
+constexpr int kStreamCells = 8;
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_scale_residual_f32(SegList L, long long nrows,
                                                                  long long per,
@@ -731,13 +745,13 @@ __global__ void __launch_bounds__(kThreads) k_scale_residual_f32(SegList L, long
     const double s = norm_of(norms, slot + R.solve);
     const int e = bits::floor_log2(s);
     const double down = pow2_floor_inv(s);
-    for (int x = sub; x < n0; x += 4 * G) {
-      double v[4];
+    for (int x = sub; x < n0; x += kStreamCells * G) {
+      double v[kStreamCells];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < kStreamCells; ++k)
         if (x + G * k < n0) v[k] = __ldg(r + x + G * k);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < kStreamCells; ++k) {
         if (x + G * k >= n0) continue;
         // the exact scaling and the rounding in integer operations where they apply
         float f;
@@ -751,7 +765,7 @@ __global__ void __launch_bounds__(kThreads) k_scale_residual_f32(SegList L, long
 
 // phi += 2^e * e32 (one rounding).  2^e * e32 is exact in binary64 (a float times a power of
 // two), so where the bit form applies one rounded addition gives the fma's result.  G lanes
-// per x-line, four cells per lane step, loads first.
+// per x-line, kStreamCells cells per lane step, loads first.
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_correct_add(SegList L, long long nrows, long long per,
                                                           const unsigned long long* norms) {
@@ -764,17 +778,17 @@ __global__ void __launch_bounds__(kThreads) k_correct_add(SegList L, long long n
     const double s = norm_of(norms, slot + R.solve);
     const int ex = bits::floor_log2(s);
     const double up = pow2_floor(s);
-    for (int x = sub; x < n0; x += 4 * G) {
-      double p[4];
-      float v[4];
+    for (int x = sub; x < n0; x += kStreamCells * G) {
+      double p[kStreamCells];
+      float v[kStreamCells];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < kStreamCells; ++k)
         if (x + G * k < n0) {
           p[k] = phi[x + G * k];
           v[k] = __ldg(e + x + G * k);
         }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < kStreamCells; ++k) {
         if (x + G * k >= n0) continue;
         double t;
         phi[x + G * k] = bits::scaled_f32_to_f64(v[k], ex, &t) ? __dadd_rn(p[k], t)
@@ -1046,7 +1060,7 @@ cudaError_t launch_maxabs_l(int dt, const SegList& L, long long nrows, unsigned 
 cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,
                                         const unsigned long long* norms, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
-  const int G = group_lanes(L.width, 4, 8, 32);  // four cells per lane
+  const int G = group_lanes(L.width, kStreamCells, 8, 32);
   const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
   if (G == 32) k_scale_residual_f32<32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
   else if (G == 16) k_scale_residual_f32<16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
@@ -1058,7 +1072,7 @@ cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,
 cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsigned long long* norms,
                                  cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
-  const int G = group_lanes(L.width, 4, 8, 32);
+  const int G = group_lanes(L.width, kStreamCells, 8, 32);
   const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
   if (G == 32) k_correct_add<32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
   else if (G == 16) k_correct_add<16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
@@ -1118,6 +1132,14 @@ cudaError_t launch_bottom(int dt, const BottomJob* jobs, int njobs, int maxN, cu
   size_t smem = (size_t)maxN * sizeof(double);
   if (dt == DT_F64) k_bottom<double><<<njobs, threads, smem, s>>>(jobs);
   else k_bottom<float><<<njobs, threads, smem, s>>>(jobs);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_valid(int dt, const DRow* rows, int nbox, long long nrows, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  Grid g = row_grid(nrows, 16);
+  GB_DISPATCH(dt, k_add_valid, g.blocks, kThreads, 0, s, one_seg(rows, nbox), nrows, g.per);
   count_launches(1);
   return cudaGetLastError();
 }
