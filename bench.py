@@ -13,11 +13,12 @@ clock record: mixed512 (512^3, FP32 inner / FP64 outer, against the FP64 solve),
 time), serving (5000 Poisson arrivals whose data lives in host memory, through
 mg_submit_host, with latency percentiles and capacity, against a one-solve-at-a-time FP64
 server), fill (the ghost-fill microbench, fused against one launch per copy tag), triad
-(the STREAM triad of the paper's Sec. 3.1-3.2, per-box launches against one launch) and the
-measured FP64 rate that the FP64 kernels' roofline uses.
+(the STREAM triad of the paper's Sec. 3.1-3.2, per-box launches against one launch), amr (a
+two-level composite solve, 128^3 coarse with the middle half refined) and the measured FP64
+rate that the FP64 kernels' roofline uses.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload dirichlet256|periodic64|mixed512|batched512|serving|fill|triad]
+                    [--workload dirichlet256|periodic64|mixed256|mixed512|batched512|serving|fill|triad|amr]
                     [--headline-only] [--kernels-only] [--no-cpu-baseline]
 
 `--workload X` prints X's line alone; `--headline-only` skips the sub-objects.
@@ -351,7 +352,8 @@ def run_ours(args, wl_name):
     if wl_name == "dirichlet256" and world == 1 and not args.headline_only:
         # the other workloads on this GPU, each with its own clock record
         for key, fn in (("mixed512", sub_mixed512), ("batched512", sub_batched),
-                        ("serving", sub_serving), ("fill", sub_fill), ("triad", sub_triad)):
+                        ("serving", sub_serving), ("amr", sub_amr), ("fill", sub_fill),
+                        ("triad", sub_triad)):
             t = time.perf_counter()
             line[key] = fn(args)
             line[key]["wall_s"] = round(time.perf_counter() - t, 1)
@@ -1057,6 +1059,96 @@ def run_fill(args):
     print(json.dumps(line), flush=True)
 
 
+def sub_amr(args, n0=128, steps=5, warmup=2):
+    """Two-level AMR composite solve: a 128^3 Dirichlet coarse level (32^3 boxes) with the
+    middle half of the domain refined by 2 (a 128^3 fine region, 32^3 boxes); lap u = f with
+    u = prod sin(pi x_d) sampled at both levels' cell centres; solved to 1e-10 with
+    mg_amr2_solve (CUDA events on the solve stream).  Reported beside it: the error against u
+    (second order: the same run at half the resolution gives about 4x the error) and the
+    oracle's composite iteration on the host cores at 16^3 (its scheme step by step)."""
+    import numpy as np
+    import torch
+    from paper_2403_12179_gb300 import inputs, mg
+    out = {"workload": "coarse 128^3 Dirichlet (32^3 boxes), region [32, 96)^3 refined by 2 "
+                       "(128^3 fine cells, 32^3 boxes), u = prod sin(pi x_d), tol 1e-10"}
+    ctx = mg.mg_init(0)
+    stream = torch.cuda.Stream()
+    mg.mg_set_stream(ctx, stream)
+
+    errs = {}
+    for n in (n0 // 2, n0):
+        f0, f1, u0, u1 = inputs.amr_sine(n, (n // 4,) * 3, (3 * n // 4,) * 3)
+        covered = np.zeros((n,) * 3, bool)
+        covered[n // 4:3 * n // 4, n // 4:3 * n // 4, n // 4:3 * n // 4] = True
+        ba0 = mg.mg_box_array_create(ctx, (0, 0, 0), (n - 1,) * 3, (32,) * 3)
+        ba1 = mg.mg_box_array_create(ctx, (n // 2,) * 3, (3 * n // 2 - 1,) * 3, (32,) * 3)
+        fr0, fr1 = _dense_to_fab(ctx, ba0, torch.from_numpy(f0).cuda(), 0, stream), \
+            _dense_to_fab(ctx, ba1, torch.from_numpy(f1).cuda(), 0, stream)
+        fp0, fp1 = mg.mg_fab_alloc(ctx, ba0, 1, 1), mg.mg_fab_alloc(ctx, ba1, 1, 1)
+        bc = mg.make_bc((0, 0, 0))
+
+        def solve():
+            mg.mg_fab_set_val(ctx, fp0, 0.0, True, stream)
+            mg.mg_fab_set_val(ctx, fp1, 0.0, True, stream)
+            return mg.mg_amr2_solve(ctx, fr0, fp0, fr1, fp1, bc, 1e-10)
+        for _ in range(warmup):
+            solve()
+        if n == n0:
+            e0, e1 = _events(steps)
+            clk = Clocks(torch.cuda.current_device())
+            res = []
+            with torch.cuda.stream(stream):
+                for i in range(steps):
+                    e0[i].record(stream)
+                    res.append(solve())
+                    e1[i].record(stream)
+            stream.synchronize()
+            clocks = clk.stop()
+            ms = [e0[i].elapsed_time(e1[i]) for i in range(steps)]
+            assert all(r.status == 0 and r.rel_resid <= 1e-10 for r in res)
+            out.update({"solves_per_s": round(1e3 / statistics.median(ms), 3),
+                        "ms_per_solve": round(statistics.median(ms), 3), "steps": steps,
+                        "iterations": res[-1].vcycles, "rel_resid": res[-1].rel_resid,
+                        "unknowns": n ** 3 - (n // 2) ** 3 + n ** 3, "clocks": clocks})
+        else:
+            r = solve()
+            assert r.status == 0
+        a0 = _fab_to_dense(ctx, fp0, u0.shape, stream).cpu().numpy()
+        a1 = _fab_to_dense(ctx, fp1, u1.shape, stream).cpu().numpy()
+        errs[n] = max(float(np.abs(a1 - u1).max()), float(np.abs((a0 - u0)[~covered]).max()))
+        for f in (fr0, fr1, fp0, fp1):
+            mg.mg_fab_free(ctx, f, stream)
+    mg.mg_finalize(ctx)
+    out["error_vs_u"] = {str(k): v for k, v in errs.items()}
+    out["error_ratio_h_over_h2"] = round(errs[n0 // 2] / errs[n0], 3)
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import amr
+        oracle.build()
+        g = amr.Geometry((16,) * 3, (4,) * 3, (12,) * 3)
+        f0, f1, _, _ = inputs.amr_sine(16, (4,) * 3, (12,) * 3)
+        t = time.perf_counter()
+        _, _, hist = amr.iterate(f0, f1, g, 9)
+        el = time.perf_counter() - t
+        out["cpu_baseline"] = {"value": round(1.0 / el, 4), "unit": "solves/s", "kind": "oracle",
+                               "cores": int(os.environ["OMP_NUM_THREADS"]),
+                               "sample": f"the oracle's composite iteration (numpy + the C++ "
+                                         f"single-level oracle), 16^3 coarse with [4, 12)^3 "
+                                         f"refined, 9 iterations to {hist[-1]:.1e}, {el:.2f} s"}
+    return out
+
+
+def run_amr(args):
+    sub = sub_amr(args)
+    line = {"metric": "two-level AMR composite solves/s to 1e-10 (128^3 coarse, middle half refined)",
+            "value": sub["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": sub["steps"],
+            "warmup": 2, "ms_per_step": sub["ms_per_solve"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "amr"}}
+    line.update(sub)
+    print(json.dumps(line), flush=True)
+
+
 # The paper's own triad timings (Sec. 3.2, one MI250X GCD), for context only
 PAPER_TRIAD = {"512x32^3": {"per_box_s": 1.16e-3, "fused_s": 3.67e-4},
                "1x256^3": {"per_box_s": 3.28e-4, "fused_s": 3.35e-4}}
@@ -1248,7 +1340,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dirichlet256",
-                    choices=sorted(WORKLOADS) + ["batched512", "serving", "fill", "triad"])
+                    choices=sorted(WORKLOADS) + ["batched512", "serving", "fill", "triad", "amr"])
     ap.add_argument("--headline-only", action="store_true",
                     help="the dirichlet256 line without the other workloads' sub-objects")
     ap.add_argument("--count", type=int, default=512, help="problems in batched512")
@@ -1267,6 +1359,8 @@ def main():
         run_fill(args)
     elif args.workload == "triad":
         run_triad(args)
+    elif args.workload == "amr":
+        run_amr(args)
     elif args.kernels_only:
         run_kernels_only(args, args.workload)
     elif args.impl == "reference":

@@ -729,8 +729,9 @@ __device__ __forceinline__ double pow2_floor_inv(double s) { return bits::pow2(-
 
 // r32 = float(r * 2^-e) with 2^e <= ||r||_inf < 2^(e+1), from the FP64 residual stored by the
 // preceding norm check (the same values the norm was taken over), and the FP32 correction's
-// initial guess e32 = 0.  G lanes per x-line, kStreamCells cells per lane step, loads first.
-constexpr int kStreamCells = 8;
+// initial guess e32 = 0.  G lanes per x-line, kScaleCells cells per lane step, loads first
+// (measured: 4 beats 8, which halves the lanes per row and the bytes per load instruction).
+constexpr int kScaleCells = 4;
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_scale_residual_f32(SegList L, long long nrows,
                                                                  long long per,
@@ -745,13 +746,13 @@ __global__ void __launch_bounds__(kThreads) k_scale_residual_f32(SegList L, long
     const double s = norm_of(norms, slot + R.solve);
     const int e = bits::floor_log2(s);
     const double down = pow2_floor_inv(s);
-    for (int x = sub; x < n0; x += kStreamCells * G) {
-      double v[kStreamCells];
+    for (int x = sub; x < n0; x += kScaleCells * G) {
+      double v[kScaleCells];
 #pragma unroll
-      for (int k = 0; k < kStreamCells; ++k)
+      for (int k = 0; k < kScaleCells; ++k)
         if (x + G * k < n0) v[k] = __ldg(r + x + G * k);
 #pragma unroll
-      for (int k = 0; k < kStreamCells; ++k) {
+      for (int k = 0; k < kScaleCells; ++k) {
         if (x + G * k >= n0) continue;
         // the exact scaling and the rounding in integer operations where they apply
         float f;
@@ -765,7 +766,9 @@ __global__ void __launch_bounds__(kThreads) k_scale_residual_f32(SegList L, long
 
 // phi += 2^e * e32 (one rounding).  2^e * e32 is exact in binary64 (a float times a power of
 // two), so where the bit form applies one rounded addition gives the fma's result.  G lanes
-// per x-line, kStreamCells cells per lane step, loads first.
+// per x-line, kCorrectCells cells per lane step, loads first (measured: 8 beats 4 here, 59
+// against 62 us at 256^3).
+constexpr int kCorrectCells = 8;
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_correct_add(SegList L, long long nrows, long long per,
                                                           const unsigned long long* norms) {
@@ -778,17 +781,17 @@ __global__ void __launch_bounds__(kThreads) k_correct_add(SegList L, long long n
     const double s = norm_of(norms, slot + R.solve);
     const int ex = bits::floor_log2(s);
     const double up = pow2_floor(s);
-    for (int x = sub; x < n0; x += kStreamCells * G) {
-      double p[kStreamCells];
-      float v[kStreamCells];
+    for (int x = sub; x < n0; x += kCorrectCells * G) {
+      double p[kCorrectCells];
+      float v[kCorrectCells];
 #pragma unroll
-      for (int k = 0; k < kStreamCells; ++k)
+      for (int k = 0; k < kCorrectCells; ++k)
         if (x + G * k < n0) {
           p[k] = phi[x + G * k];
           v[k] = __ldg(e + x + G * k);
         }
 #pragma unroll
-      for (int k = 0; k < kStreamCells; ++k) {
+      for (int k = 0; k < kCorrectCells; ++k) {
         if (x + G * k >= n0) continue;
         double t;
         phi[x + G * k] = bits::scaled_f32_to_f64(v[k], ex, &t) ? __dadd_rn(p[k], t)
@@ -1060,7 +1063,7 @@ cudaError_t launch_maxabs_l(int dt, const SegList& L, long long nrows, unsigned 
 cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,
                                         const unsigned long long* norms, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
-  const int G = group_lanes(L.width, kStreamCells, 8, 32);
+  const int G = group_lanes(L.width, kScaleCells, 8, 32);
   const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
   if (G == 32) k_scale_residual_f32<32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
   else if (G == 16) k_scale_residual_f32<16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
@@ -1072,7 +1075,7 @@ cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,
 cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsigned long long* norms,
                                  cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
-  const int G = group_lanes(L.width, kStreamCells, 8, 32);
+  const int G = group_lanes(L.width, kCorrectCells, 8, 32);
   const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
   if (G == 32) k_correct_add<32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
   else if (G == 16) k_correct_add<16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);

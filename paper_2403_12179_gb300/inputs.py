@@ -117,6 +117,24 @@ def gaussian_blobs(n: int = 512, seed: int = 5, nblob: int = 16, noise: float = 
     return np.ascontiguousarray(out)
 
 
+def amr_sine(n0: int, A, B):
+    """A two-level problem with known solution: level 0 covers the unit cube with n0^3
+    cells, level 1 the coarse box region [A, B) refined by 2.  Returns (f0, f1, u0, u1):
+    f = -3 pi^2 u and u = prod sin(pi x_d) at the cell centres of each level (dense arrays
+    (nz, ny, nx); level 1 spans the refined region only)."""
+    h0 = 1.0 / n0
+    x0 = centers(n0)
+    xs = [(np.arange(2 * (B[d] - A[d])) + 0.5) * (h0 / 2) + A[d] * h0 for d in range(3)]
+
+    def field(xx, yy, zz):
+        s = [np.sin(PI * v) for v in (xx, yy, zz)]
+        return s[2][:, None, None] * s[1][None, :, None] * s[0][None, None, :]
+    u0 = field(x0, x0, x0)
+    u1 = field(*xs)
+    return (np.ascontiguousarray(-3 * PI * PI * u0), np.ascontiguousarray(-3 * PI * PI * u1),
+            np.ascontiguousarray(u0), np.ascontiguousarray(u1))
+
+
 @dataclasses.dataclass
 class Request:
     t_arrive: float

@@ -28,3 +28,19 @@ def test_serving_mix_follows_the_recipe():
         assert abs(np.mean(ns == n) - p) < 0.03
     assert abs(np.mean([r.periodic for r in reqs]) - 0.5) < 0.03
     assert set(r.box for r in reqs) <= {32, 64}
+
+
+def test_amr_sine_closed_form():
+    """The two-level manufactured problem: u = prod sin(pi x_d) at each level's cell
+    centres (level 1 over the refined region, half the cell size) and f = -3 pi^2 u."""
+    n0, A, B = 8, (2, 1, 3), (6, 5, 7)
+    f0, f1, u0, u1 = inputs.amr_sine(n0, A, B)
+    assert u0.shape == (8, 8, 8) and u1.shape == (8, 8, 8)
+    h0 = 1.0 / n0
+    i, j, k = 3, 5, 6
+    assert np.isclose(u0[k, j, i], np.sin(np.pi * (i + .5) * h0) * np.sin(np.pi * (j + .5) * h0) *
+                      np.sin(np.pi * (k + .5) * h0), rtol=0, atol=1e-15)
+    x = [A[d] * h0 + (v + .5) * h0 / 2 for d, v in enumerate((i, j, k))]
+    assert np.isclose(u1[k, j, i], np.prod(np.sin(np.pi * np.array(x))), rtol=0, atol=1e-15)
+    assert np.allclose(f1, -3 * np.pi ** 2 * u1, rtol=1e-15, atol=0)
+    assert np.allclose(f0, -3 * np.pi ** 2 * u0, rtol=1e-15, atol=0)
