@@ -52,6 +52,10 @@ struct Member {
   int64_t own_ba = 0, own_rhs = 0, own_phi = 0;
   std::string ws_key;
   double* phi_host = nullptr;
+  cudaEvent_t copied = nullptr;  // host-memory requests: the copy in (or out) has finished
+  ~Member() {
+    if (copied) cudaEventDestroy(copied);
+  }
 };
 
 // Segment-list builders (host side); offsets into the step's packed upload.
@@ -565,20 +569,37 @@ bool take_idle(Ctx::Server& S, const std::string& key, Member& m) {
   return false;
 }
 
+// Publishes a finished member's result.
+void publish(Ctx::Server& S, Member& m) {
+  // counted with the publication, so a caller that has polled every ticket sees them all
+  std::lock_guard<std::mutex> lk(S.mu);
+  S.done[m.ticket] = m.res;
+  S.stats.completed += 1;
+  S.cv_done.notify_all();
+}
+
 void server_loop(Ctx* c) {
   Ctx::Server& S = *c->server;
   cudaSetDevice(c->device);
   cudaStream_t s = c->stream;
+  // Host-memory requests copy in and out on their own stream, so that the copies of some
+  // requests overlap the shared steps of the others: a request joins the steps once its copy
+  // in has finished, and completes once its copy out has.
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) cs = s;
   Staging st;
-  std::vector<std::unique_ptr<Member>> active;
+  std::vector<std::unique_ptr<Member>> active, loading, unloading;
   std::vector<int> free_slots;
   int nslots = 0;
   for (;;) {
     std::vector<Ctx::Server::Req> admit;
     {
       std::unique_lock<std::mutex> lk(S.mu);
-      if (active.empty())
-        S.cv_work.wait(lk, [&] { return S.stop || S.trim || !S.queue.empty(); });
+      auto ready = [&] { return S.stop || S.trim || !S.queue.empty(); };
+      if (active.empty()) {
+        if (loading.empty() && unloading.empty()) S.cv_work.wait(lk, ready);
+        else S.cv_work.wait_for(lk, std::chrono::microseconds(100), ready);
+      }
       if (S.trim) {
         while (evict_idle(*c, S, s)) {
         }
@@ -586,9 +607,11 @@ void server_loop(Ctx* c) {
         S.trim = false;
         S.cv_done.notify_all();
       }
-      if (S.stop && S.queue.empty() && active.empty()) break;
+      if (S.stop && S.queue.empty() && active.empty() && loading.empty() && unloading.empty())
+        break;
       // admission: while a slot is free (pool room is checked when the hierarchy is built)
-      while (!S.queue.empty() && (int)(active.size() + admit.size()) < S.max_active) {
+      while (!S.queue.empty() &&
+             (int)(active.size() + loading.size() + admit.size()) < S.max_active) {
         admit.push_back(S.queue.front());
         S.queue.pop_front();
       }
@@ -631,10 +654,12 @@ void server_loop(Ctx* c) {
           }
           rid = m->own_rhs;
           pid = m->own_phi;
-          dense_upload(*c, *c->get_fab(rid), r.rhs_host, s);
+          dense_upload(*c, *c->get_fab(rid), r.rhs_host, cs);
           auto fp = c->get_fab(pid);
-          if (r.phi_is_guess) dense_upload(*c, *fp, r.phi_host, s);
-          else MG_CK(cudaMemsetAsync(fp->base, 0, fp->bytes, s));
+          if (r.phi_is_guess) dense_upload(*c, *fp, r.phi_host, cs);
+          else MG_CK(cudaMemsetAsync(fp->base, 0, fp->bytes, cs));
+          MG_CK(cudaEventCreateWithFlags(&m->copied, cudaEventDisableTiming));
+          MG_CK(cudaEventRecord(m->copied, cs));
         }
         auto fr = c->get_fab(rid);
         auto fp = c->get_fab(pid);
@@ -643,6 +668,7 @@ void server_loop(Ctx* c) {
         for (auto& h : c->hier)
           if (h.get() == &H) m->H = h;
       } catch (const MgError& e) {
+        cudaStreamSynchronize(cs);  // a copy in may have started
         release_own(*c, *m, s);
         if (e.code == MG_ENOMEM && !active.empty()) {
           // no room: back to the head of the queue until a running solve retires
@@ -653,20 +679,50 @@ void server_loop(Ctx* c) {
         m->status = e.code;
         m->done = true;
         finish(*c, *m);
-        std::lock_guard<std::mutex> lk(S.mu);
-        S.done[m->ticket] = m->res;
-        S.stats.completed += 1;
-        S.cv_done.notify_all();
+        publish(S, *m);
         continue;
       }
-      if (free_slots.empty()) {
-        free_slots.push_back(nslots);
-        nslots += 2;
+      if (m->copied) loading.push_back(std::move(m));  // joins once its data is in
+      else {
+        if (free_slots.empty()) {
+          free_slots.push_back(nslots);
+          nslots += 2;
+        }
+        m->slot = free_slots.back();
+        free_slots.pop_back();
+        fresh_members.push_back(m.get());
+        active.push_back(std::move(m));
       }
-      m->slot = free_slots.back();
-      free_slots.pop_back();
-      fresh_members.push_back(m.get());
-      active.push_back(std::move(m));
+    }
+    // members whose copy in has finished join this step
+    {
+      std::vector<std::unique_ptr<Member>> still;
+      for (auto& m : loading) {
+        const cudaError_t q = cudaEventQuery(m->copied);
+        if (q == cudaErrorNotReady) {
+          still.push_back(std::move(m));
+          continue;
+        }
+        if (q != cudaSuccess) {
+          cudaGetLastError();
+          cudaStreamSynchronize(cs);
+          m->status = MG_ECUDA;
+          m->done = true;
+          finish(*c, *m);
+          release_own(*c, *m, s);
+          publish(S, *m);
+          continue;
+        }
+        if (free_slots.empty()) {
+          free_slots.push_back(nslots);
+          nslots += 2;
+        }
+        m->slot = free_slots.back();
+        free_slots.pop_back();
+        fresh_members.push_back(m.get());
+        active.push_back(std::move(m));
+      }
+      loading.swap(still);
     }
     {
       std::lock_guard<std::mutex> lk(S.mu);
@@ -724,51 +780,69 @@ void server_loop(Ctx* c) {
       leaving.push_back(std::move(m));
     }
     active.swap(keep);
-    // host-memory requests: the answer goes back to the caller's array before completion
-    bool any_host = false;
-    for (auto& m : leaving)
-      if (m->own_phi) {
-        try {
-          if (m->phi_host)
-            dense_download(*c, *c->get_fab(m->own_phi), m->phi_host, s);
-        } catch (const MgError& e) {
-          if (m->res.status == MG_OK) m->res.status = e.code;
-        }
-        any_host = true;
-      }
-    if (any_host) {
-      if (cudaStreamSynchronize(s) != cudaSuccess)
-        for (auto& m : leaving)
-          if (m->own_phi && m->res.status == MG_OK) m->res.status = MG_ECUDA;
-      for (auto& m : leaving)
-        if (m->own_phi) {
-          m->res.t_end = c->now();
-          m->res.seconds = m->res.t_end - m->res.t_start;
-          if (m->res.status == MG_OK || m->res.status == MG_NOT_CONVERGED) {
-            S.idle.push_back({m->ws_key, m->own_ba, m->own_rhs, m->own_phi});
-            m->own_ba = m->own_rhs = m->own_phi = 0;
-          } else {
-            release_own(*c, *m, s);
-          }
-        }
+    // host-memory requests: the answer goes back to the caller's array (on the copy stream,
+    // after the steps that produced it) before completion; the others complete now
+    if (!leaving.empty() && cs != s) {
+      cudaEvent_t stepped;
+      MG_CK(cudaEventCreateWithFlags(&stepped, cudaEventDisableTiming));
+      MG_CK(cudaEventRecord(stepped, s));
+      MG_CK(cudaStreamWaitEvent(cs, stepped, 0));
+      cudaEventDestroy(stepped);
     }
     for (auto& m : leaving) {
-      // counted with the publication, so a caller that has polled every ticket sees them all
-      std::lock_guard<std::mutex> lk(S.mu);
-      S.done[m->ticket] = m->res;
-      S.stats.completed += 1;
-      S.cv_done.notify_all();
+      if (!m->own_phi) {
+        publish(S, *m);
+        continue;
+      }
+      try {
+        if (m->phi_host) dense_download(*c, *c->get_fab(m->own_phi), m->phi_host, cs);
+        if (!m->copied) MG_CK(cudaEventCreateWithFlags(&m->copied, cudaEventDisableTiming));
+        MG_CK(cudaEventRecord(m->copied, cs));
+        unloading.push_back(std::move(m));
+      } catch (const MgError& e) {
+        if (m->res.status == MG_OK) m->res.status = e.code;
+        cudaStreamSynchronize(cs);
+        release_own(*c, *m, s);
+        publish(S, *m);
+      }
+    }
+    // copies out that have finished: the request completes, its workspace turns idle
+    {
+      std::vector<std::unique_ptr<Member>> still;
+      for (auto& m : unloading) {
+        const cudaError_t q = cudaEventQuery(m->copied);
+        if (q == cudaErrorNotReady) {
+          still.push_back(std::move(m));
+          continue;
+        }
+        if (q != cudaSuccess) {
+          cudaGetLastError();
+          if (m->res.status == MG_OK) m->res.status = MG_ECUDA;
+        }
+        m->res.t_end = c->now();
+        m->res.seconds = m->res.t_end - m->res.t_start;
+        if (m->res.status == MG_OK || m->res.status == MG_NOT_CONVERGED) {
+          S.idle.push_back({m->ws_key, m->own_ba, m->own_rhs, m->own_phi});
+          m->own_ba = m->own_rhs = m->own_phi = 0;
+        } else {
+          release_own(*c, *m, s);
+        }
+        publish(S, *m);
+      }
+      unloading.swap(still);
     }
     {
       std::lock_guard<std::mutex> lk(S.mu);
       S.stats.retire_seconds += secs_since(t_ret0);
     }
   }
+  cudaStreamSynchronize(cs);
   while (evict_idle(*c, S, s)) {
   }
   if (st.dev) st.dev->reset(s);
   for (NormBuf& nb : S.norms) nb.release(s);
   cudaStreamSynchronize(s);
+  if (cs != s) cudaStreamDestroy(cs);
 }
 
 }  // namespace
