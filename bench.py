@@ -665,7 +665,9 @@ def sub_batched(args, steps=3, warmup=1):
         for _ in range(max(1, warmup)):
             batch(prec)
         clk = Clocks(torch.cuda.current_device())
+        torch.cuda.nvtx.range_push(f"timed_{name}")  # (lets a profiler keep these runs only)
         runs = [batch(prec) for _ in range(steps)]
+        torch.cuda.nvtx.range_pop()
         clocks[name] = clk.stop()
         out[name] = statistics.median(r[0] for r in runs)
         vcs[name] = [r.vcycles for r in runs[-1][1]]

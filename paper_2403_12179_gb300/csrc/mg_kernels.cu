@@ -298,6 +298,48 @@ __global__ void __launch_bounds__(256) k_copy_tags(TagList L, long long nchunks,
   }
 }
 
+// The same fill for fabs of 2 to 4 components (NC = 4): every component's loads of a lane's
+// U cells are issued before any store, and cell offsets are kept as 32-bit offsets from the
+// tag's first source / destination cell (fewer registers, more resident warps).
+template <class T>
+__global__ void __launch_bounds__(256, 3) k_copy_tags_multi(TagList L, long long nchunks,
+                                                            int ncomp) {
+  constexpr int U = kTagChunkN / 32;
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (w >= nchunks) return;
+  const int lane = threadIdx.x & 31;
+  TagSeg S = L.one;
+  if (L.n > 1) S = L.segs[find_tagseg(L.segs, L.n, w)];
+  const int2 ch = S.chunks[w - S.chunk_begin];
+  const DTag t = S.tags[ch.x];
+  const int r1 = min(ch.y + tag_chunk_rows(t.ex, ncomp), t.ey * t.ez);
+  const int ncell = (r1 - ch.y) * t.ex;
+  const T* __restrict__ src = (const T*)S.base + t.src;
+  T* __restrict__ dst = (T*)S.base + t.dst;
+  for (int i0 = lane; i0 < ncell; i0 += 32 * U) {
+    int so[U], d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = min(i0 + 32 * u, ncell - 1);  // tail lanes repeat the last cell
+      const int x = i % t.ex, r = ch.y + i / t.ex;
+      const int y = r % t.ey, z = r / t.ey;
+      so[u] = x * t.ssx + y * t.ssy + z * t.ssz;
+      d[u] = x + y * t.dsy + z * t.dsz;
+    }
+    T v[4][U];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        v[c][u] = c < ncomp ? tag_value(src + so[u] + c * t.scs, t.sign) : T(0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (c < ncomp) dst[d[u] + c * t.dcs] = v[c][u];
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Flush per-warp maxima: each warp stores (slot, max); thread 0 merges equal slots.
 __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
@@ -868,11 +910,16 @@ int num_sms() {
 cudaError_t launch_copy_tags_l(int dt, const TagList& L, long long nchunks, int ncomp, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
   unsigned blocks = (unsigned)((nchunks + 7) / 8);
+  // 2 to 4 components: all components' loads first (measured on the 4-component microbench:
+  // 99 us against 120 us per fill)
+  const bool multi = ncomp > 1 && ncomp <= 4;
   if (dt == DT_F64) {
     if (ncomp == 1) k_copy_tags<double, 1><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
+    else if (multi) k_copy_tags_multi<double><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
     else k_copy_tags<double, 0><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
   } else {
     if (ncomp == 1) k_copy_tags<float, 1><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
+    else if (multi) k_copy_tags_multi<float><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
     else k_copy_tags<float, 0><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
   }
   count_launches(1);
