@@ -67,6 +67,7 @@ constexpr double kN0 = 8.0 / 15.0, kN1 = 2.0 / 3.0, kN2 = -1.0 / 5.0;
 __global__ void __launch_bounds__(256) k_cf_ghosts(const CFGhost* __restrict__ T, int n,
                                                    double* __restrict__ fine,
                                                    const double* __restrict__ coarse) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const CFGhost& e = T[i];
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(256) k_reflux(const RefluxCell* __restrict__ T
                                                 const double* __restrict__ coarse,
                                                 const double* __restrict__ fine, double ih0,
                                                 double ih1) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const RefluxCell& e = T[i];
@@ -386,7 +388,7 @@ AmrPlan& get_plan(Ctx& c, int64_t rhs0, int64_t phi0, int64_t rhs1, int64_t phi1
 void fill_fine(Ctx& c, AmrPlan& P, FabObj& f0, FabObj& f1, cudaStream_t s) {
   launch_fill(c, f1, &P.fine_bc, s, 1);
   if (P.ncf) {
-    k_cf_ghosts<<<(P.ncf + 255) / 256, 256, 0, s>>>((const CFGhost*)P.cf->p, P.ncf,
+    launch_k(k_cf_ghosts, (P.ncf + 255) / 256, 256, 0, s, (const CFGhost*)P.cf->p, P.ncf,
                                                     (double*)f1.base, (const double*)f0.base);
     count_launches(1);
     MG_CK(cudaGetLastError());
@@ -406,7 +408,7 @@ void enqueue_residual(Ctx& c, AmrPlan& P, cudaStream_t s) {
   MG_CK(launch_residual(DT_F64, P.coarse_resid.rows(), P.coarse_resid.nbox,
                         P.coarse_resid.nrows, nullptr, s));
   if (P.nrf) {
-    k_reflux<<<(P.nrf + 255) / 256, 256, 0, s>>>((const RefluxCell*)P.rf->p, P.nrf,
+    launch_k(k_reflux, (P.nrf + 255) / 256, 256, 0, s, (const RefluxCell*)P.rf->p, P.nrf,
                                                   (double*)r0->base, (const double*)f0->base,
                                                   (const double*)f1->base, 1.0 / P.h0, 1.0 / P.h1);
     count_launches(1);

@@ -167,6 +167,7 @@ __device__ void bottom(const Lev<T> B, const double* __restrict__ Mt, int N) {
 // 512 threads for FP64 (128 registers each), 1024 for FP32.
 template <class T>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024, 1) k_coarse_cycle(const CoarseJob* __restrict__ jobs) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Lev<T> L[kMaxCoarseLevels];
   const CoarseJob& J = jobs[blockIdx.x];
@@ -247,8 +248,8 @@ cudaError_t launch_coarse_cycle(int dt, const CoarseJob* jobs, int njobs, size_t
   if (smem > kCoarseSmemMax) return cudaErrorInvalidValue;
   cudaError_t e = coarse_opt_in(dt, smem);
   if (e != cudaSuccess) return e;
-  if (dt == DT_F64) k_coarse_cycle<double><<<njobs, 512, smem, s>>>(jobs);
-  else k_coarse_cycle<float><<<njobs, 1024, smem, s>>>(jobs);
+  if (dt == DT_F64) launch_k(k_coarse_cycle<double>, njobs, 512, smem, s, jobs);
+  else launch_k(k_coarse_cycle<float>, njobs, 1024, smem, s, jobs);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_rbgs_fused(UnitList L, int ty
                                                               unsigned phi_buf_elems,
                                                               unsigned rhs_buf_elems,
                                                               int* __restrict__ err) {
+  pdl_begin();
   constexpr int NP = 4 + D;  // live phi planes s-2..s+1 plus D in flight
   constexpr int NR = RS ? 2 + D : 0;  // live rhs planes s-1, s plus D in flight
   extern __shared__ __align__(128) unsigned char smem[];
@@ -442,7 +443,7 @@ static cudaError_t launch_fused_t(const UnitList& L, long long nunits, int ty, i
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = opt_in_smem((const void*)k_rbgs_fused<T, D, RS>, smem);
   if (e != cudaSuccess) return e;
-  k_rbgs_fused<T, D, RS><<<(unsigned)nunits, kFusedThreads, smem, s>>>(L, ty, pe, re, err);
+  launch_k(k_rbgs_fused<T, D, RS>, (unsigned)nunits, kFusedThreads, smem, s, L, ty, pe, re, err);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -266,6 +266,7 @@ __device__ __forceinline__ T tag_value(const T* p, int sign) {
 // bandwidth).  NC = 1: one component; NC = 0: ncomp components.
 template <class T, int NC>
 __global__ void __launch_bounds__(256) k_copy_tags(TagList L, long long nchunks, int ncomp) {
+  pdl_begin();
   constexpr int U = (NC == 1 ? kTagChunk1 : kTagChunkN) / 32;
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (w >= nchunks) return;
@@ -304,6 +305,7 @@ __global__ void __launch_bounds__(256) k_copy_tags(TagList L, long long nchunks,
 template <class T>
 __global__ void __launch_bounds__(256, 3) k_copy_tags_multi(TagList L, long long nchunks,
                                                             int ncomp) {
+  pdl_begin();
   constexpr int U = kTagChunkN / 32;
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (w >= nchunks) return;
@@ -381,14 +383,23 @@ __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
 // MODE 2 (same conditions): the max-norm of the residual of every updated cell just BEFORE
 // its update -- the neighbour sum of the update is exactly the one that residual needs,
 // Dirichlet reads included, since they read the cell's value before the update -- and the
-// value before the update saved to v[2] (same layout as phi), so that the half-sweep can be
-// undone (k_restore_colour).
+// value before the update saved to v[2], so that the half-sweep can be undone
+// (k_restore_colour).
+// MODE 3 (same conditions, no norm): the residual of every updated cell just after its update
+// (as MODE 1 takes it) stored to v[2], for the residual + restriction that follows
+// (k_residual_restrict with STORED).
+// v[2] of MODE 2 / 3 is a one-colour view: cell x of row (y, z) at element x / 2 of the row
+// (two cells of one colour are never neighbours in x), so that a warp's stores fill whole
+// sectors instead of every other element of sectors it has not read.
 // Resident blocks per SM the half-sweep is built for (register budget): the norm variants
 // hold more live values.
+// (Measured on GB300 at 256^3: 3 blocks per SM for the norm / store variants, without
+// spills, made the solve 1% slower than 4 with a few spilled registers.)
 constexpr int kSweepMinBlocks = 4, kNormMinBlocks = 4;
 template <class T, bool DIRECT, int MODE, int G>
 __global__ void __launch_bounds__(kThreads, MODE ? kNormMinBlocks : kSweepMinBlocks)
     k_rbgs_half(SegList L, long long nrows, long long per, int color, unsigned long long* norms) {
+  pdl_begin();
   // A lane updates cells x and x + 2G of a pair step together (both of this colour: their
   // neighbours are of the other colour and unchanged, so both loads go first -- two
   // independent FP64 chains per lane).
@@ -400,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, MODE ? kNormMinBlocks : kSweepMinBlo
     const int y = (int)lr % n1, z = (int)lr / n1;
     T* phi = line<T>(R.v[0], y, z);
     const T* rhs = line<T>(R.v[1], y, z);
-    T* save = MODE == 2 ? line<T>(R.v[2], y, z) : nullptr;
+    T* save = MODE >= 2 ? line<T>(R.v[2], y, z) : nullptr;  // saved values / residuals
     const T h2 = level_const<T>(R.h2), ih2 = level_const<T>(R.ih2);
     const int par = (color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1;
     cur = slot + R.solve;
@@ -424,18 +435,20 @@ __global__ void __launch_bounds__(kThreads, MODE ? kNormMinBlocks : kSweepMinBlo
         const T u1 = gs_update(s1, r1, h2);
         if (MODE == 2) {
           norm(s1, o1, r1);
-          save[x] = o1;
+          save[x >> 1] = o1;
         }
         phi[x] = u1;
         if (MODE == 1) norm(resum(x, s1), u1, r1);
+        if (MODE == 3) save[x >> 1] = residual_of(resum(x, s1), u1, r1, ih2);
         if (two) {
           const T u2 = gs_update(s2, r2, h2);
           if (MODE == 2) {
             norm(s2, o2, r2);
-            save[x2] = o2;
+            save[x2 >> 1] = o2;
           }
           phi[x2] = u2;
           if (MODE == 1) norm(resum(x2, s2), u2, r2);
+          if (MODE == 3) save[x2 >> 1] = residual_of(resum(x2, s2), u2, r2, ih2);
         }
       }
     };
@@ -454,14 +467,15 @@ __global__ void __launch_bounds__(kThreads, MODE ? kNormMinBlocks : kSweepMinBlo
       sweep([&](int x) { return nbr_sum(phi + x, pitch, plane); }, [](int, T s) { return s; });
     }
   });
-  if (MODE) flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
+  if (MODE == 1 || MODE == 2) flush_block_max(Ar<T>::key_to_f64bits(warp_max(mx)), cur, norms);
 }
 
 // Undo of a MODE 2 half-sweep: cells of colour `color` take back their saved values
-// (v[0] = phi, v[2] = the saved values).
+// (v[0] = phi, v[2] = the saved values, one-colour view).
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_restore_colour(SegList L, long long nrows, long long per,
                                                              int color) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
@@ -469,7 +483,7 @@ __global__ void __launch_bounds__(kThreads) k_restore_colour(SegList L, long lon
     T* phi = line<T>(R.v[0], y, z);
     const T* save = line<T>(R.v[2], y, z);
     const int par = (color + R.lo[0] + R.lo[1] + y + R.lo[2] + z) & 1;
-    for (int x = par + 2 * lane; x < n0; x += 64) phi[x] = save[x];
+    for (int x = par + 2 * lane; x < n0; x += 64) phi[x] = save[x >> 1];
   });
 }
 
@@ -478,6 +492,7 @@ __global__ void __launch_bounds__(kThreads) k_restore_colour(SegList L, long lon
 template <class T, bool DIRECT>
 __global__ void __launch_bounds__(kThreads, DIRECT ? 4 : 6) k_residual(SegList L, long long nrows, long long per,
                                                        unsigned long long* norms, int color) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   unsigned long long mx = 0;
   int cur = -1;
@@ -523,9 +538,13 @@ __global__ void __launch_bounds__(kThreads, DIRECT ? 4 : 6) k_residual(SegList L
 // Fused residual + restriction.  G lanes per coarse x-line (32, or fewer for narrow boxes):
 // lane l produces coarse cells X = l, l+G, ...: the 8 child residuals summed x fastest,
 // times 1/8.
-template <class T, bool DIRECT, int G>
+// STORED: the children of colour 1 (black) take the residual that the preceding black
+// half-sweep stored in v[2] (k_rbgs_half MODE 3, the same value; one-colour view, so that
+// the black child of fine row (2Y + j, 2Z + k) is element X) instead of computing it.
+template <class T, bool DIRECT, int G, bool STORED = false>
 __global__ void __launch_bounds__(kThreads) k_residual_restrict(SegList L, long long nrows,
                                                                 long long per) {
+  pdl_begin();
   const int lane = threadIdx.x & (G - 1);
   for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int nc0 = R.n[0] >> 1, nc1 = R.n[1] >> 1;
@@ -545,11 +564,16 @@ __global__ void __launch_bounds__(kThreads) k_residual_restrict(SegList L, long 
           const Nbr<T> nb = DIRECT ? nbr_rows<T>(R, row, 2 * Y + j, 2 * Z + k) : Nbr<T>{};
 #pragma unroll
           for (int i = 0; i < 2; ++i) {
-            const T* q = line<T>(vr, 2 * Y + j, 2 * Z + k) + 2 * X + i;
-            T s = !DIRECT ? nbr_sum(row + 2 * X + i, vp.pitch, vp.plane)
-                          : (nb.neg & 60u) ? nbr_sum_rows<true>(row, 2 * X + i, n0, nb)
-                                           : nbr_sum_rows<false>(row, 2 * X + i, n0, nb);
-            T v = residual_of(s, row[2 * X + i], q[0], ih2);
+            T v;
+            if (STORED && ((R.lo[0] + R.lo[1] + R.lo[2] + i + j + k) & 1)) {
+              v = line<T>(R.v[2], 2 * Y + j, 2 * Z + k)[X];
+            } else {
+              const T* q = line<T>(vr, 2 * Y + j, 2 * Z + k) + 2 * X + i;
+              T s = !DIRECT ? nbr_sum(row + 2 * X + i, vp.pitch, vp.plane)
+                            : (nb.neg & 60u) ? nbr_sum_rows<true>(row, 2 * X + i, n0, nb)
+                                             : nbr_sum_rows<false>(row, 2 * X + i, n0, nb);
+              v = residual_of(s, row[2 * X + i], q[0], ih2);
+            }
             acc = (i | j | k) ? Ar<T>::add(acc, v) : v;
           }
         }
@@ -561,6 +585,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_restrict(SegList L, long 
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_restrict(SegList L, long long nrows, long long per) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int nc0 = R.n[0] >> 1, nc1 = R.n[1] >> 1;
@@ -586,6 +611,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(SegList L, long long nrow
 // fine x-line.
 template <class T, int G>
 __global__ void __launch_bounds__(kThreads) k_prolong_add(SegList L, long long nrows, long long per) {
+  pdl_begin();
   const int lane = threadIdx.x & (G - 1);
   for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
@@ -607,6 +633,7 @@ __device__ __forceinline__ T lerp34(T a, T b) {
 }
 template <class T, int G>
 __global__ void __launch_bounds__(kThreads) k_prolong_trilinear(SegList L, long long nrows, long long per) {
+  pdl_begin();
   const int lane = threadIdx.x & (G - 1);
   for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
@@ -632,6 +659,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_trilinear(SegList L, long 
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_set_valid(SegList L, long long nrows, long long per,
                                                         T value) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
@@ -645,6 +673,7 @@ __global__ void __launch_bounds__(kThreads) k_set_valid(SegList L, long long nro
 // run either as one launch over all boxes or as one launch per box.  G lanes per x-line.
 template <class T, int G>
 __global__ void __launch_bounds__(kThreads) k_triad(SegList L, long long nrows, long long per, T s) {
+  pdl_begin();
   const int lane = threadIdx.x & (G - 1);
   for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
@@ -662,6 +691,7 @@ __global__ void __launch_bounds__(kThreads) k_triad(SegList L, long long nrows, 
 __device__ double g_probe_sink;
 constexpr int kProbeChains = 8;
 __global__ void __launch_bounds__(256) k_fp64_probe(int iters, double b, double c) {
+  pdl_begin();
   double a[kProbeChains];
 #pragma unroll
   for (int k = 0; k < kProbeChains; ++k) a[k] = 1e-3 * threadIdx.x + k;
@@ -678,6 +708,7 @@ __global__ void __launch_bounds__(256) k_fp64_probe(int iters, double b, double 
 // a += b on valid cells: v[0] = a, v[1] = b.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_add_valid(SegList L, long long nrows, long long per) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
     const int n0 = R.n[0], n1 = R.n[1];
@@ -690,6 +721,7 @@ __global__ void __launch_bounds__(kThreads) k_add_valid(SegList L, long long nro
 
 template <class T>
 __global__ void k_set_flat(T* p, long long n, T value) {
+  pdl_begin();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     p[i] = value;
@@ -698,6 +730,7 @@ __global__ void k_set_flat(T* p, long long n, T value) {
 // Exact bottom solve: one block per job, rhs gathered to shared memory in FP64.
 template <class T>
 __global__ void k_bottom(const BottomJob* __restrict__ jobs) {
+  pdl_begin();
   extern __shared__ double sb[];
   const BottomJob J = jobs[blockIdx.x];
   const T* rhs = (const T*)J.rhs;
@@ -715,6 +748,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_dense_copy(SegList L, long long nrows, long long per,
                                                          T* dense, int3 dlo, int3 dn, int ncomp,
                                                          int to_dense) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   const long long dplane = (long long)dn.x * dn.y, dcomp = dplane * dn.z;
   for_rows(L, nrows, per, [&](const DRow& R, long long lr, int) {
@@ -738,6 +772,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_copy(SegList L, long long nr
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_maxabs(SegList L, long long nrows, long long per,
                                                      unsigned long long* norms) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   unsigned long long mx = 0;
   int cur = -1;
@@ -778,6 +813,7 @@ template <int G>
 __global__ void __launch_bounds__(kThreads) k_scale_residual_f32(SegList L, long long nrows,
                                                                  long long per,
                                                                  const unsigned long long* norms) {
+  pdl_begin();
   const int sub = threadIdx.x & (G - 1);
   for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
     const int n0 = R.n[0], n1 = R.n[1];
@@ -814,6 +850,7 @@ constexpr int kCorrectCells = 8;
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_correct_add(SegList L, long long nrows, long long per,
                                                           const unsigned long long* norms) {
+  pdl_begin();
   const int sub = threadIdx.x & (G - 1);
   for_rows<32 / G>(L, nrows, per, [&](const DRow& R, long long lr, int slot) {
     const int n0 = R.n[0], n1 = R.n[1];
@@ -864,6 +901,13 @@ Grid row_grid(long long nrows, int blocks_per_sm, int rows_per_pass = kWarps) {
 
 static std::atomic<long long> g_launches{0};
 void count_launches(long long n) { g_launches += n; }
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("GBMG_NO_PDL");
+    return !(e && e[0] == '1');
+  }();
+  return on;
+}
 long long launches_so_far() { return g_launches.load(); }
 
 cudaError_t opt_in_smem(const void* kernel, size_t smem) {
@@ -893,17 +937,17 @@ int num_sms() {
 
 #define GB_DISPATCH(dt, KERNEL, GRID, BLOCK, SMEM, STREAM, ...)                       \
   do {                                                                                 \
-    if ((dt) == DT_F64) KERNEL<double><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);    \
-    else KERNEL<float><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);                    \
+    if ((dt) == DT_F64) launch_k(KERNEL<double>, GRID, BLOCK, SMEM, STREAM, __VA_ARGS__);    \
+    else launch_k(KERNEL<float>, GRID, BLOCK, SMEM, STREAM, __VA_ARGS__);                    \
   } while (0)
 #define GB_DISPATCH_D(dt, direct, KERNEL, GRID, BLOCK, SMEM, STREAM, ...)                  \
   do {                                                                                   \
     if ((dt) == DT_F64) {                                                                \
-      if (direct) KERNEL<double, true><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);       \
-      else KERNEL<double, false><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);             \
+      if (direct) launch_k(KERNEL<double, true>, GRID, BLOCK, SMEM, STREAM, __VA_ARGS__);       \
+      else launch_k(KERNEL<double, false>, GRID, BLOCK, SMEM, STREAM, __VA_ARGS__);             \
     } else {                                                                             \
-      if (direct) KERNEL<float, true><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);        \
-      else KERNEL<float, false><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__);              \
+      if (direct) launch_k(KERNEL<float, true>, GRID, BLOCK, SMEM, STREAM, __VA_ARGS__);        \
+      else launch_k(KERNEL<float, false>, GRID, BLOCK, SMEM, STREAM, __VA_ARGS__);              \
     }                                                                                    \
   } while (0)
 
@@ -914,13 +958,13 @@ cudaError_t launch_copy_tags_l(int dt, const TagList& L, long long nchunks, int 
   // 99 us against 120 us per fill)
   const bool multi = ncomp > 1 && ncomp <= 4;
   if (dt == DT_F64) {
-    if (ncomp == 1) k_copy_tags<double, 1><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
-    else if (multi) k_copy_tags_multi<double><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
-    else k_copy_tags<double, 0><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
+    if (ncomp == 1) launch_k(k_copy_tags<double, 1>, blocks, 256, 0, s, L, nchunks, ncomp);
+    else if (multi) launch_k(k_copy_tags_multi<double>, blocks, 256, 0, s, L, nchunks, ncomp);
+    else launch_k(k_copy_tags<double, 0>, blocks, 256, 0, s, L, nchunks, ncomp);
   } else {
-    if (ncomp == 1) k_copy_tags<float, 1><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
-    else if (multi) k_copy_tags_multi<float><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
-    else k_copy_tags<float, 0><<<blocks, 256, 0, s>>>(L, nchunks, ncomp);
+    if (ncomp == 1) launch_k(k_copy_tags<float, 1>, blocks, 256, 0, s, L, nchunks, ncomp);
+    else if (multi) launch_k(k_copy_tags_multi<float>, blocks, 256, 0, s, L, nchunks, ncomp);
+    else launch_k(k_copy_tags<float, 0>, blocks, 256, 0, s, L, nchunks, ncomp);
   }
   count_launches(1);
   return cudaGetLastError();
@@ -956,15 +1000,15 @@ int group_lanes(int width, int cells, int lo, int hi) {
 template <class T, bool DIRECT>
 void rbgs_half_g(int G, const Grid& g, cudaStream_t s, const SegList& L, long long nrows, int color,
                  unsigned long long* norms) {
-  if (G == 16) k_rbgs_half<T, DIRECT, 0, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
-  else if (G == 8) k_rbgs_half<T, DIRECT, 0, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
-  else k_rbgs_half<T, DIRECT, 0, 4><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+  if (G == 16) launch_k(k_rbgs_half<T, DIRECT, 0, 16>, g.blocks, kThreads, 0, s, L, nrows, g.per, color, norms);
+  else if (G == 8) launch_k(k_rbgs_half<T, DIRECT, 0, 8>, g.blocks, kThreads, 0, s, L, nrows, g.per, color, norms);
+  else launch_k(k_rbgs_half<T, DIRECT, 0, 4>, g.blocks, kThreads, 0, s, L, nrows, g.per, color, norms);
 }
 template <class T, int MODE>
 void rbgs_half_norm_g(int G, const Grid& g, cudaStream_t s, const SegList& L, long long nrows, int color,
                       unsigned long long* norms) {
-  if (G == 16) k_rbgs_half<T, true, MODE, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
-  else k_rbgs_half<T, true, MODE, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, color, norms);
+  if (G == 16) launch_k(k_rbgs_half<T, true, MODE, 16>, g.blocks, kThreads, 0, s, L, nrows, g.per, color, norms);
+  else launch_k(k_rbgs_half<T, true, MODE, 8>, g.blocks, kThreads, 0, s, L, nrows, g.per, color, norms);
 }
 }  // namespace
 
@@ -1007,23 +1051,32 @@ cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigne
 namespace {
 template <class T, bool DIRECT>
 void residual_restrict_g(int G, const Grid& g, cudaStream_t s, const SegList& L, long long nrows) {
-  if (G == 32) k_residual_restrict<T, DIRECT, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
-  else if (G == 16) k_residual_restrict<T, DIRECT, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
-  else k_residual_restrict<T, DIRECT, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+  if (G == 32) launch_k(k_residual_restrict<T, DIRECT, 32>, g.blocks, kThreads, 0, s, L, nrows, g.per);
+  else if (G == 16) launch_k(k_residual_restrict<T, DIRECT, 16>, g.blocks, kThreads, 0, s, L, nrows, g.per);
+  else launch_k(k_residual_restrict<T, DIRECT, 8>, g.blocks, kThreads, 0, s, L, nrows, g.per);
 }
 template <class T>
 void prolong_add_g(int G, const Grid& g, cudaStream_t s, const SegList& L, long long nrows) {
-  if (G == 32) k_prolong_add<T, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
-  else if (G == 16) k_prolong_add<T, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
-  else k_prolong_add<T, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+  if (G == 32) launch_k(k_prolong_add<T, 32>, g.blocks, kThreads, 0, s, L, nrows, g.per);
+  else if (G == 16) launch_k(k_prolong_add<T, 16>, g.blocks, kThreads, 0, s, L, nrows, g.per);
+  else launch_k(k_prolong_add<T, 8>, g.blocks, kThreads, 0, s, L, nrows, g.per);
 }
 }  // namespace
 
-cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s, bool direct) {
+cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s,
+                                       bool direct, bool stored) {
   if (nrows <= 0) return cudaSuccess;
   // rows are coarse lines of width / 2 cells, one per lane
   const int G = group_lanes(L.width, 2, 8, 32);
   const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  if (stored) {
+    if (dt != DT_F64 || !direct) return cudaErrorInvalidValue;
+    if (G == 32) launch_k(k_residual_restrict<double, true, 32, true>, g.blocks, kThreads, 0, s, L, nrows, g.per);
+    else if (G == 16) launch_k(k_residual_restrict<double, true, 16, true>, g.blocks, kThreads, 0, s, L, nrows, g.per);
+    else launch_k(k_residual_restrict<double, true, 8, true>, g.blocks, kThreads, 0, s, L, nrows, g.per);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   if (dt == DT_F64) {
     if (direct) residual_restrict_g<double, true>(G, g, s, L, nrows);
     else residual_restrict_g<double, false>(G, g, s, L, nrows);
@@ -1040,13 +1093,13 @@ cudaError_t launch_prolong_trilinear_l(int dt, const SegList& L, long long nrows
   const int G = group_lanes(L.width, 1, 8, 32);
   const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
   if (dt == DT_F64) {
-    if (G == 32) k_prolong_trilinear<double, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
-    else if (G == 16) k_prolong_trilinear<double, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
-    else k_prolong_trilinear<double, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+    if (G == 32) launch_k(k_prolong_trilinear<double, 32>, g.blocks, kThreads, 0, s, L, nrows, g.per);
+    else if (G == 16) launch_k(k_prolong_trilinear<double, 16>, g.blocks, kThreads, 0, s, L, nrows, g.per);
+    else launch_k(k_prolong_trilinear<double, 8>, g.blocks, kThreads, 0, s, L, nrows, g.per);
   } else {
-    if (G == 32) k_prolong_trilinear<float, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
-    else if (G == 16) k_prolong_trilinear<float, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
-    else k_prolong_trilinear<float, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per);
+    if (G == 32) launch_k(k_prolong_trilinear<float, 32>, g.blocks, kThreads, 0, s, L, nrows, g.per);
+    else if (G == 16) launch_k(k_prolong_trilinear<float, 16>, g.blocks, kThreads, 0, s, L, nrows, g.per);
+    else launch_k(k_prolong_trilinear<float, 8>, g.blocks, kThreads, 0, s, L, nrows, g.per);
   }
   count_launches(1);
   return cudaGetLastError();
@@ -1067,14 +1120,14 @@ cudaError_t launch_triad_l(int dt, const SegList& L, long long nrows, double sc,
   const int G = group_lanes(L.width, 1, 8, 32);
   const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
   if (dt == DT_F64) {
-    if (G == 32) k_triad<double, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, sc);
-    else if (G == 16) k_triad<double, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, sc);
-    else k_triad<double, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, sc);
+    if (G == 32) launch_k(k_triad<double, 32>, g.blocks, kThreads, 0, s, L, nrows, g.per, sc);
+    else if (G == 16) launch_k(k_triad<double, 16>, g.blocks, kThreads, 0, s, L, nrows, g.per, sc);
+    else launch_k(k_triad<double, 8>, g.blocks, kThreads, 0, s, L, nrows, g.per, sc);
   } else {
     const float f = (float)sc;
-    if (G == 32) k_triad<float, 32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, f);
-    else if (G == 16) k_triad<float, 16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, f);
-    else k_triad<float, 8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, f);
+    if (G == 32) launch_k(k_triad<float, 32>, g.blocks, kThreads, 0, s, L, nrows, g.per, f);
+    else if (G == 16) launch_k(k_triad<float, 16>, g.blocks, kThreads, 0, s, L, nrows, g.per, f);
+    else launch_k(k_triad<float, 8>, g.blocks, kThreads, 0, s, L, nrows, g.per, f);
   }
   count_launches(1);
   return cudaGetLastError();
@@ -1083,7 +1136,7 @@ cudaError_t launch_triad_l(int dt, const SegList& L, long long nrows, double sc,
 cudaError_t launch_fp64_probe(int iters, long long* lane_ops, cudaStream_t s) {
   if (iters < 1) return cudaErrorInvalidValue;
   const int blocks = num_sms() * 8;
-  k_fp64_probe<<<blocks, 256, 0, s>>>(iters, 0.999999, 1e-7);
+  launch_k(k_fp64_probe, blocks, 256, 0, s, iters, 0.999999, 1e-7);
   if (lane_ops) *lane_ops = (long long)blocks * 256 * kProbeChains * iters;
   count_launches(1);
   return cudaGetLastError();
@@ -1092,8 +1145,8 @@ cudaError_t launch_fp64_probe(int iters, long long* lane_ops, cudaStream_t s) {
 cudaError_t launch_set_valid_l(int dt, const SegList& L, long long nrows, double value, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   Grid g = row_grid(nrows, 16);
-  if (dt == DT_F64) k_set_valid<double><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, value);
-  else k_set_valid<float><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, (float)value);
+  if (dt == DT_F64) launch_k(k_set_valid<double>, g.blocks, kThreads, 0, s, L, nrows, g.per, value);
+  else launch_k(k_set_valid<float>, g.blocks, kThreads, 0, s, L, nrows, g.per, (float)value);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1112,9 +1165,9 @@ cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,
   if (nrows <= 0) return cudaSuccess;
   const int G = group_lanes(L.width, kScaleCells, 8, 32);
   const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
-  if (G == 32) k_scale_residual_f32<32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
-  else if (G == 16) k_scale_residual_f32<16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
-  else k_scale_residual_f32<8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
+  if (G == 32) launch_k(k_scale_residual_f32<32>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
+  else if (G == 16) launch_k(k_scale_residual_f32<16>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
+  else launch_k(k_scale_residual_f32<8>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1124,9 +1177,9 @@ cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsign
   if (nrows <= 0) return cudaSuccess;
   const int G = group_lanes(L.width, kCorrectCells, 8, 32);
   const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
-  if (G == 32) k_correct_add<32><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
-  else if (G == 16) k_correct_add<16><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
-  else k_correct_add<8><<<g.blocks, kThreads, 0, s>>>(L, nrows, g.per, norms);
+  if (G == 32) launch_k(k_correct_add<32>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
+  else if (G == 16) launch_k(k_correct_add<16>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
+  else launch_k(k_correct_add<8>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1154,8 +1207,19 @@ cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
 }
 
 cudaError_t launch_residual_restrict(int dt, const DRow* rows, int nbox, long long nrows,
-                                     cudaStream_t s, bool direct, int width) {
-  return launch_residual_restrict_l(dt, one_seg(rows, nbox, 0, width), nrows, s, direct);
+                                     cudaStream_t s, bool direct, int width, bool stored) {
+  return launch_residual_restrict_l(dt, one_seg(rows, nbox, 0, width), nrows, s, direct, stored);
+}
+
+cudaError_t launch_rbgs_half_store(const DRow* rows, int nbox, long long nrows, int color,
+                                   cudaStream_t s, int width) {
+  if (nrows <= 0) return cudaSuccess;
+  const SegList L = one_seg(rows, nbox, 0, width);
+  const int G = group_lanes(L.width, 4, 8, 16);
+  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  rbgs_half_norm_g<double, 3>(G, g, s, L, nrows, color, nullptr);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows, cudaStream_t s) {
@@ -1180,8 +1244,8 @@ cudaError_t launch_bottom(int dt, const BottomJob* jobs, int njobs, int maxN, cu
   if (njobs <= 0) return cudaSuccess;
   int threads = maxN < 32 ? 32 : (maxN > 1024 ? 1024 : (maxN + 31) / 32 * 32);
   size_t smem = (size_t)maxN * sizeof(double);
-  if (dt == DT_F64) k_bottom<double><<<njobs, threads, smem, s>>>(jobs);
-  else k_bottom<float><<<njobs, threads, smem, s>>>(jobs);
+  if (dt == DT_F64) launch_k(k_bottom<double>, njobs, threads, smem, s, jobs);
+  else launch_k(k_bottom<float>, njobs, threads, smem, s, jobs);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1204,8 +1268,8 @@ cudaError_t launch_set_flat(int dt, void* p, long long n, double value, cudaStre
   long long blocks = (n + 255) / 256;
   long long cap = (long long)num_sms() * 8;
   if (blocks > cap) blocks = cap;
-  if (dt == DT_F64) k_set_flat<double><<<(unsigned)blocks, 256, 0, s>>>((double*)p, n, value);
-  else k_set_flat<float><<<(unsigned)blocks, 256, 0, s>>>((float*)p, n, (float)value);
+  if (dt == DT_F64) launch_k(k_set_flat<double>, (unsigned)blocks, 256, 0, s, (double*)p, n, value);
+  else launch_k(k_set_flat<float>, (unsigned)blocks, 256, 0, s, (float*)p, n, (float)value);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1218,9 +1282,9 @@ cudaError_t launch_dense_copy(int dt, const DRow* rows, int nbox, long long nrow
   int3 lo = make_int3(dom_lo[0], dom_lo[1], dom_lo[2]);
   int3 n = make_int3(dom_n[0], dom_n[1], dom_n[2]);
   if (dt == DT_F64)
-    k_dense_copy<double><<<g.blocks, kThreads, 0, s>>>(one_seg(rows, nbox), nrows, g.per, (double*)dense, lo, n, ncomp, to_dense);
+    launch_k(k_dense_copy<double>, g.blocks, kThreads, 0, s, one_seg(rows, nbox), nrows, g.per, (double*)dense, lo, n, ncomp, to_dense);
   else
-    k_dense_copy<float><<<g.blocks, kThreads, 0, s>>>(one_seg(rows, nbox), nrows, g.per, (float*)dense, lo, n, ncomp, to_dense);
+    launch_k(k_dense_copy<float>, g.blocks, kThreads, 0, s, one_seg(rows, nbox), nrows, g.per, (float*)dense, lo, n, ncomp, to_dense);
   count_launches(1);
   return cudaGetLastError();
 }

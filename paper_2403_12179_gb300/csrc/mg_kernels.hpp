@@ -172,6 +172,39 @@ cudaError_t opt_in_smem(const void* kernel, size_t smem);
 void count_launches(long long n);
 long long launches_so_far();
 
+// Programmatic dependent launch.  Every kernel of this library is launched through launch_k,
+// which lets the GPU start launching it as the blocks of the kernel before it in the stream
+// exit, and begins with pdl_begin(): wait until that kernel has completed and its writes are
+// visible.  The stencil chains of a V-cycle are hundreds of dependent launches, many of them
+// a few microseconds long on the coarse levels, so the launch latency would otherwise sit
+// between every two of them.  No kernel triggers its dependents early: a trigger at kernel
+// start (so that the next kernel's blocks wait on the SMs) made every measured solve slower
+// (256^3 FP64 1.1%, 512^3 mixed 4%), while the implicit trigger at block exit gives the 64^3
+// solve 5% and the 256^3 one 0.2% (GB300).  Results do not depend on it (the wait comes
+// before any memory access); GBMG_NO_PDL=1 in the environment launches without the
+// attribute.
+bool pdl_enabled();
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+template <class... P, class... A>
+inline void launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     A&&... a) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(a)...);  // errors: cudaGetLastError()
+}
+#endif
+
 cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int nchunks,
                              void* base, int ncomp, cudaStream_t s);
 
@@ -183,12 +216,14 @@ cudaError_t launch_copy_tags(int dt, const DTag* tags, const int2* chunks, int n
 // box array's periodic extents are even).  width: the widest box x-extent of the table
 // (0 = unknown; any value gives the same results, it only picks the lanes per row).
 // pre = true (needs norms): the norm is that of each updated cell's residual just before its
-// update, and the values before the update are saved to v[2] (same layout as v[0]) so that
+// update, and the values before the update are saved to v[2] (a one-colour view: cell x of
+// row (y, z) at element x / 2 of that row; row pitch and plane of its own) so that
 // launch_restore_colour can undo the half-sweep.
 cudaError_t launch_rbgs_half(int dt, const DRow* rows, int nbox, long long nrows, int color,
                              cudaStream_t s, bool direct = false,
                              unsigned long long* norms = nullptr, int width = 0, bool pre = false);
-// v[0] = phi, v[2] = saved values: cells of colour `color` take their saved values back.
+// v[0] = phi, v[2] = saved values (one-colour view): cells of colour `color` take their
+// saved values back.
 cudaError_t launch_restore_colour(int dt, const DRow* rows, int nbox, long long nrows, int color,
                                   cudaStream_t s);
 
@@ -200,9 +235,16 @@ cudaError_t launch_residual(int dt, const DRow* rows, int nbox, long long nrows,
                             int color = -1);
 
 // Rows are coarse x-lines.  v[0] = phi, v[1] = rhs (fine); c[0] = coarse rhs,
-// c[1] = coarse phi (p == null: not zeroed).
+// c[1] = coarse phi (p == null: not zeroed).  stored (FP64, direct): the fine cells of colour
+// 1 take the residual in v[2] (one-colour view) that launch_rbgs_half_store left there.
 cudaError_t launch_residual_restrict(int dt, const DRow* rows, int nbox, long long nrows,
-                                     cudaStream_t s, bool direct = false, int width = 0);
+                                     cudaStream_t s, bool direct = false, int width = 0,
+                                     bool stored = false);
+// FP64 half-sweep (direct reads, one table) that also stores, in v[2] (one-colour view), the
+// residual of every cell it updates just after its update (the values a residual pass would
+// compute next).
+cudaError_t launch_rbgs_half_store(const DRow* rows, int nbox, long long nrows, int color,
+                                   cudaStream_t s, int width);
 
 // Rows are coarse x-lines.  v[0] = fine field; c[0] = coarse field.
 cudaError_t launch_restrict(int dt, const DRow* rows, int nbox, long long nrows, cudaStream_t s);
@@ -275,7 +317,7 @@ cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int co
 cudaError_t launch_residual_l(int dt, const SegList& L, long long nrows, unsigned long long* norms,
                               cudaStream_t s, bool direct = false, int color = -1);
 cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows, cudaStream_t s,
-                                       bool direct = false);
+                                       bool direct = false, bool stored = false);
 cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cudaStream_t s);
 cudaError_t launch_prolong_trilinear_l(int dt, const SegList& L, long long nrows, cudaStream_t s);
 cudaError_t launch_set_valid_l(int dt, const SegList& L, long long nrows, double value, cudaStream_t s);

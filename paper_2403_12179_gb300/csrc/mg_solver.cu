@@ -310,18 +310,59 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
               H->L[0].direct && H->direct0;
     for (int d = 0; d < 3; ++d)
       if (per[d] && (lev[0].dom.len(d) & 1)) ok = false;
+    LevelData& D = H->L[0];
+    const BoxArray& ba = D.bao->ba;
+    // one-colour arrays over the level-0 boxes: (nx + 1) / 2 elements a row, rows dense
+    std::vector<long long> off(ba.boxes.size() + 1, 0);
+    for (size_t b = 0; b < ba.boxes.size(); ++b) {
+      const Box& B = ba.boxes[b];
+      off[b + 1] = off[b] + (long long)((B.len(0) + 1) / 2) * B.len(1) * B.len(2);
+    }
+    auto half_view = [&](const DevBufP& buf, int b) {
+      const Box& B = ba.boxes[b];
+      DView v{};
+      v.pitch = (B.len(0) + 1) / 2;
+      v.plane = (long long)v.pitch * B.len(1);
+      v.cstride = v.plane * B.len(2);
+      v.p = (double*)buf->p + off[b];
+      return v;
+    };
     if (ok) {
-      LevelData& D = H->L[0];
-      H->save0 = internal_fab(c, phi.ba, phi.lay.g, DT_F64);
+      H->save0 = c.alloc((size_t)off.back() * 8, s);
       FaceReads fr = direct_neighbours(*D.phi, per);
       D.smooth.d->reset(s);
-      D.smooth = make_table(c, D.bao->ba, 0, D.h, 0, [&](int b, DRow& R) {
+      D.smooth = make_table(c, ba, 0, D.h, 0, [&](int b, DRow& R) {
         R.v[0] = D.phi->view(b);
         R.v[1] = D.rhs->view(b);
-        R.v[2] = H->save0->view(b);
+        R.v[2] = half_view(H->save0, b);
         fr.apply(b, R);
       }, s);
       D.smooth.direct = true;
+    }
+    // the last pre-smoothing half-sweep stores the black cells' residuals for the residual +
+    // restriction, when level 0 is restricted by a stage kernel (not the bottom solve's level)
+    if (ok && std::min(H->lc, nl - 1) >= 1) {
+      H->res0 = c.alloc((size_t)off.back() * 8, s);
+      FaceReads fr = direct_neighbours(*D.phi, per);
+      const LevelData& C = H->L[1];
+      H->store0 = make_table(c, ba, 0, D.h, 0, [&](int b, DRow& R) {
+        R.v[0] = D.phi->view(b);
+        R.v[1] = D.rhs->view(b);
+        R.v[2] = half_view(H->res0, b);
+        fr.apply(b, R);
+      }, s);
+      H->store0.direct = true;
+      D.rr.d->reset(s);
+      D.rr = make_table(c, ba, 1, D.h, 0, [&](int b, DRow& R) {
+        R.v[0] = D.phi->view(b);
+        R.v[1] = D.rhs->view(b);
+        R.v[2] = half_view(H->res0, b);
+        R.c[0] = coarse_view_of(*C.rhs, ba.boxes[b]);
+        R.c[1] = coarse_view_of(*C.phi, ba.boxes[b]);
+        fr.apply(b, R);
+      }, s);
+      D.rr.direct = true;
+      H->stored0 = true;
     }
   }
   H->dnorm = c.alloc(16, s);
@@ -333,10 +374,12 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
 namespace {
 
 // last_norm != null: the final (black) half-sweep also accumulates the residual max-norm of
-// the cells it updates there (the caller adds the red cells).
+// the cells it updates there (the caller adds the red cells).  store_last: the final (black)
+// half-sweep also stores the residuals of the cells it updates (level 0: H.store0), for the
+// residual + restriction that follows.
 void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s,
             unsigned long long* last_norm = nullptr, bool time_first = false,
-            bool skip_first_red = false) {
+            bool skip_first_red = false, bool store_last = false) {
   int k = 0;
   if (D.fused) {
     // pairs of fused sweeps: phi -> phi2 -> phi
@@ -355,8 +398,12 @@ void smooth(Ctx& c, Hierarchy& H, LevelData& D, int sweeps, cudaStream_t s,
       const bool timed = time_first && k == 0 && color == 1;
       // (external records: captured into the step graph as event-record nodes)
       if (timed) MG_CK(cudaEventRecordWithFlags(H.sweep_ev[0], s, cudaEventRecordExternal));
-      MG_CK(launch_rbgs_half(H.dt, D.smooth.rows(), D.smooth.nbox, D.smooth.nrows, color, s,
-                             D.direct, last ? last_norm : nullptr, D.smooth.width));
+      if (last && store_last)
+        MG_CK(launch_rbgs_half_store(H.store0.rows(), H.store0.nbox, H.store0.nrows, color, s,
+                                     H.store0.width));
+      else
+        MG_CK(launch_rbgs_half(H.dt, D.smooth.rows(), D.smooth.nbox, D.smooth.nrows, color, s,
+                               D.direct, last ? last_norm : nullptr, D.smooth.width));
       if (timed) MG_CK(cudaEventRecordWithFlags(H.sweep_ev[1], s, cudaEventRecordExternal));
     }
 }
@@ -368,10 +415,14 @@ void enqueue_vcycle(Ctx& c, Hierarchy& H, cudaStream_t s, unsigned long long* no
   for (int l = 0; l < top; ++l) {
     LevelData& D = H.L[l];
     if (D.fused) launch_fill(c, *D.rhs, &H.bc, s, 1);  // rhs ghosts for the redundant ring
-    smooth(c, H, D, H.p.nu1, s, nullptr, l == 0 && H.graph_timed, l == 0 && skip_first_red);
+    // the finest level with res0 (FP64, direct reads, half-sweeps): the black children's
+    // residuals come from the last pre-smoothing half-sweep
+    const bool stored = l == 0 && H.stored0;
+    smooth(c, H, D, H.p.nu1, s, nullptr, l == 0 && H.graph_timed, l == 0 && skip_first_red,
+           stored);
     if (!D.direct) launch_fill(c, *D.phi, &H.bc, s, 1);
     MG_CK(launch_residual_restrict(H.dt, D.rr.rows(), D.rr.nbox, D.rr.nrows, s, D.direct,
-                                   D.rr.width));
+                                   D.rr.width, stored));
   }
   if (H.lc < nl) MG_CK(launch_coarse_cycle(H.dt, (const CoarseJob*)H.cjob->p, 1, H.csmem, s));
   else MG_CK(launch_bottom(H.dt, (const BottomJob*)H.job->p, 1, H.N, s));

@@ -47,7 +47,13 @@ struct Hierarchy {
   // iterate (it computes the same neighbour sums), replacing a separate residual pass; it
   // runs speculatively at the end of each step, saving the red values it replaces in save0
   // (null when the solve does not speculate), and is undone if the stop test ends the solve.
-  std::shared_ptr<FabObj> save0;
+  // res0 holds, within each V-cycle, the black cells' residuals that the last pre-smoothing
+  // half-sweep stores for the residual + restriction (stored0: level 0's residual +
+  // restriction table reads them; store0 is that half-sweep's table).  Both are one-colour
+  // arrays (half a row per row, see launch_rbgs_half).
+  DevBufP save0, res0;
+  OpTable store0;
+  bool stored0 = false;
   // step graphs: [0] plain step, [1] first step of a speculating solve (a whole V-cycle,
   // then the next one's red half-sweep), [2] later steps (the V-cycle without that red
   // half-sweep, then the next one's)
