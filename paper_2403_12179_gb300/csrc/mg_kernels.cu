@@ -986,6 +986,13 @@ namespace {
 // Blocks per SM the stencil row kernels aim for (measured: 16 beats 8 and 4 on both the
 // finest and the coarser levels).
 constexpr int kRowBlocksPerSM = 16;
+// Launches over boxes at most 32 cells wide (rows of a pass or two per block) take twice as
+// many, smaller blocks: measured on GB300, 512 batched problems of 32^3 boxes 2045 -> 2090
+// solves/s and the 512 x 32^3 triad 126 -> 120 us, with the 256^3 solve unchanged (4 or 8
+// blocks per SM made both slower).
+inline int row_blocks_per_sm(int width) {
+  return width > 0 && width <= 32 ? 2 * kRowBlocksPerSM : kRowBlocksPerSM;
+}
 
 // Lanes per x-line for a launch whose widest line holds `width` cells (0 = unknown): the
 // smallest group (of those the kernels are built for) whose lanes each get `cells`
@@ -1019,7 +1026,7 @@ cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int co
   if (pre && !norms) return cudaErrorInvalidValue;
   // a line of w cells holds w / 2 of one colour; two per lane
   const int G = group_lanes(L.width, 4, norms ? 8 : 4, 16);
-  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  const Grid g = row_grid(nrows, row_blocks_per_sm(L.width), kWarps * (32 / G));
   if (norms) {
     if (dt == DT_F64) {
       if (pre) rbgs_half_norm_g<double, 2>(G, g, s, L, nrows, color, norms);
@@ -1068,7 +1075,7 @@ cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows
   if (nrows <= 0) return cudaSuccess;
   // rows are coarse lines of width / 2 cells, one per lane
   const int G = group_lanes(L.width, 2, 8, 32);
-  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  const Grid g = row_grid(nrows, row_blocks_per_sm(L.width), kWarps * (32 / G));
   if (stored) {
     if (dt != DT_F64 || !direct) return cudaErrorInvalidValue;
     if (G == 32) launch_k(k_residual_restrict<double, true, 32, true>, g.blocks, kThreads, 0, s, L, nrows, g.per);
@@ -1091,7 +1098,7 @@ cudaError_t launch_residual_restrict_l(int dt, const SegList& L, long long nrows
 cudaError_t launch_prolong_trilinear_l(int dt, const SegList& L, long long nrows, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   const int G = group_lanes(L.width, 1, 8, 32);
-  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  const Grid g = row_grid(nrows, row_blocks_per_sm(L.width), kWarps * (32 / G));
   if (dt == DT_F64) {
     if (G == 32) launch_k(k_prolong_trilinear<double, 32>, g.blocks, kThreads, 0, s, L, nrows, g.per);
     else if (G == 16) launch_k(k_prolong_trilinear<double, 16>, g.blocks, kThreads, 0, s, L, nrows, g.per);
@@ -1108,7 +1115,7 @@ cudaError_t launch_prolong_trilinear_l(int dt, const SegList& L, long long nrows
 cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   const int G = group_lanes(L.width, 1, 8, 32);
-  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  const Grid g = row_grid(nrows, row_blocks_per_sm(L.width), kWarps * (32 / G));
   if (dt == DT_F64) prolong_add_g<double>(G, g, s, L, nrows);
   else prolong_add_g<float>(G, g, s, L, nrows);
   count_launches(1);
@@ -1118,7 +1125,7 @@ cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cuda
 cudaError_t launch_triad_l(int dt, const SegList& L, long long nrows, double sc, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   const int G = group_lanes(L.width, 1, 8, 32);
-  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  const Grid g = row_grid(nrows, row_blocks_per_sm(L.width), kWarps * (32 / G));
   if (dt == DT_F64) {
     if (G == 32) launch_k(k_triad<double, 32>, g.blocks, kThreads, 0, s, L, nrows, g.per, sc);
     else if (G == 16) launch_k(k_triad<double, 16>, g.blocks, kThreads, 0, s, L, nrows, g.per, sc);
@@ -1164,7 +1171,7 @@ cudaError_t launch_scale_residual_f32_l(const SegList& L, long long nrows,
                                         const unsigned long long* norms, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   const int G = group_lanes(L.width, kScaleCells, 8, 32);
-  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  const Grid g = row_grid(nrows, row_blocks_per_sm(L.width), kWarps * (32 / G));
   if (G == 32) launch_k(k_scale_residual_f32<32>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
   else if (G == 16) launch_k(k_scale_residual_f32<16>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
   else launch_k(k_scale_residual_f32<8>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
@@ -1176,7 +1183,7 @@ cudaError_t launch_correct_add_l(const SegList& L, long long nrows, const unsign
                                  cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   const int G = group_lanes(L.width, kCorrectCells, 8, 32);
-  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  const Grid g = row_grid(nrows, row_blocks_per_sm(L.width), kWarps * (32 / G));
   if (G == 32) launch_k(k_correct_add<32>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
   else if (G == 16) launch_k(k_correct_add<16>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
   else launch_k(k_correct_add<8>, g.blocks, kThreads, 0, s, L, nrows, g.per, norms);
@@ -1216,7 +1223,7 @@ cudaError_t launch_rbgs_half_store(const DRow* rows, int nbox, long long nrows, 
   if (nrows <= 0) return cudaSuccess;
   const SegList L = one_seg(rows, nbox, 0, width);
   const int G = group_lanes(L.width, 4, 8, 16);
-  const Grid g = row_grid(nrows, kRowBlocksPerSM, kWarps * (32 / G));
+  const Grid g = row_grid(nrows, row_blocks_per_sm(L.width), kWarps * (32 / G));
   rbgs_half_norm_g<double, 3>(G, g, s, L, nrows, color, nullptr);
   count_launches(1);
   return cudaGetLastError();
