@@ -631,7 +631,27 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(SegList L, long long n
     const int ox = R.lo[0] & 1, oy = R.lo[1] & 1, oz = R.lo[2] & 1;
     T* f = line<T>(R.v[0], y, z);
     const T* c = line<T>(R.c[0], (y + oy) >> 1, (z + oz) >> 1);
-    for (int x = lane; x < n0; x += G) f[x] = Ar<T>::add(f[x], c[(x + ox) >> 1]);
+    if constexpr (sizeof(T) == 4) {
+      // FP32: four cells of a lane per step, all loads first (measured on GB300: 512
+      // batched problems 2242 -> 2345 solves/s; the FP64 form keeps one cell per step, as
+      // four made the 256^3 FP64 solve 3% slower)
+      for (int x = lane; x < n0; x += 4 * G) {
+        T a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int xq = x + G * q;
+          a[q] = xq < n0 ? f[xq] : T(0);
+          b[q] = xq < n0 ? c[(xq + ox) >> 1] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int xq = x + G * q;
+          if (xq < n0) f[xq] = Ar<T>::add(a[q], b[q]);
+        }
+      }
+    } else {
+      for (int x = lane; x < n0; x += G) f[x] = Ar<T>::add(f[x], c[(x + ox) >> 1]);
+    }
   });
 }
 
@@ -1126,7 +1146,7 @@ cudaError_t launch_prolong_trilinear_l(int dt, const SegList& L, long long nrows
 
 cudaError_t launch_prolong_add_l(int dt, const SegList& L, long long nrows, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
-  const int G = group_lanes(L.width, 1, 8, 32);
+  const int G = group_lanes(L.width, dt == DT_F64 ? 1 : 4, 8, 32);  // cells per lane step
   const Grid g = row_grid(nrows, row_blocks_per_sm(L.width), kWarps * (32 / G));
   if (dt == DT_F64) prolong_add_g<double>(G, g, s, L, nrows);
   else prolong_add_g<float>(G, g, s, L, nrows);
