@@ -118,11 +118,18 @@ struct AmrPlan {
   std::shared_ptr<Hierarchy> H;    // single-level cycle on (r0, e0)
   DevBufP cf, rf;
   int ncf = 0, nrf = 0;
+  bool fine_direct = false, coarse_direct = false;  // tables read neighbouring boxes directly
   OpTable fine_smooth, fine_resid, coarse_resid, coarse_copy_f, fine_copy_f, avg_down,
       restrict_r, prolong, add0, rmax0, rmax1;
   DevBufP dnorm;
   unsigned long long* hnorm = nullptr;
+  // one composite iteration (correction, fine sweeps, average-down, residual + norm) as a
+  // CUDA graph, captured on `graph_stream` with `graph_kernels` kernels
+  cudaGraphExec_t step = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  long long graph_kernels = 0;
   ~AmrPlan() {
+    if (step) cudaGraphExecDestroy(step);
     if (hnorm) cudaFreeHost(hnorm);
   }
 };
@@ -330,20 +337,30 @@ AmrPlan& get_plan(Ctx& c, int64_t rhs0, int64_t phi0, int64_t rhs1, int64_t phi1
   }
   P->nrf = (int)rf.size();
   P->rf = c.upload(rf.data(), rf.size() * sizeof(RefluxCell), s);
-  // level tables
+  // level tables.  On a regular grid of fine boxes the fine stencils read neighbouring fine
+  // boxes directly and only the coarse/fine ghosts of the region's faces (written by
+  // k_cf_ghosts) as ghost cells; the coarse residual reads neighbouring boxes directly too.
+  const int no_periodic[3] = {0, 0, 0};
+  const FaceReads frf = direct_neighbours(*f1, no_periodic, true);
+  const FaceReads frc = direct_neighbours(*f0, per);
+  P->fine_direct = frf.ok();
+  P->coarse_direct = frc.ok();
   P->fine_smooth = make_table(c, F, 0, P->h1, 0, [&](int b, DRow& R) {
     R.v[0] = f1->view(b);
     R.v[1] = g1->view(b);
+    frf.apply(b, R);
   }, s);
   P->fine_resid = make_table(c, F, 0, P->h1, 0, [&](int b, DRow& R) {
     R.v[0] = f1->view(b);
     R.v[1] = g1->view(b);
     R.v[2] = r1->view(b);
+    frf.apply(b, R);
   }, s);
   P->coarse_resid = make_table(c, C, 0, P->h0, 0, [&](int b, DRow& R) {
     R.v[0] = f0->view(b);
     R.v[1] = g0->view(b);
     R.v[2] = r0->view(b);
+    frc.apply(b, R);
   }, s);
   P->coarse_copy_f = make_table(c, C, 0, P->h0, 0, [&](int b, DRow& R) {
     R.v[0] = r0->view(b);
@@ -386,7 +403,7 @@ AmrPlan& get_plan(Ctx& c, int64_t rhs0, int64_t phi0, int64_t rhs1, int64_t phi1
 
 // Coarse/fine ghosts of phi1 from phi0 (after the fine level's own fill).
 void fill_fine(Ctx& c, AmrPlan& P, FabObj& f0, FabObj& f1, cudaStream_t s) {
-  launch_fill(c, f1, &P.fine_bc, s, 1);
+  if (!P.fine_direct) launch_fill(c, f1, &P.fine_bc, s, 1);
   if (P.ncf) {
     launch_k(k_cf_ghosts, (P.ncf + 255) / 256, 256, 0, s, (const CFGhost*)P.cf->p, P.ncf,
                                                     (double*)f1.base, (const double*)f0.base);
@@ -403,10 +420,10 @@ void enqueue_residual(Ctx& c, AmrPlan& P, cudaStream_t s) {
   unsigned long long* dn = (unsigned long long*)P.dnorm->p;
   fill_fine(c, P, *f0, *f1, s);
   MG_CK(launch_residual(DT_F64, P.fine_resid.rows(), P.fine_resid.nbox, P.fine_resid.nrows,
-                        nullptr, s));
-  launch_fill(c, *f0, &P.bc, s, 1);
+                        nullptr, s, P.fine_direct));
+  if (!P.coarse_direct) launch_fill(c, *f0, &P.bc, s, 1);
   MG_CK(launch_residual(DT_F64, P.coarse_resid.rows(), P.coarse_resid.nbox,
-                        P.coarse_resid.nrows, nullptr, s));
+                        P.coarse_resid.nrows, nullptr, s, P.coarse_direct));
   if (P.nrf) {
     launch_k(k_reflux, (P.nrf + 255) / 256, 256, 0, s, (const RefluxCell*)P.rf->p, P.nrf,
                                                   (double*)r0->base, (const double*)f0->base,
@@ -431,6 +448,10 @@ double bits2d(unsigned long long b) {
 namespace {
 void release_plan(Ctx& c, AmrPlan& P) {
   cudaStreamSynchronize(c.stream);
+  if (P.step) {
+    cudaGraphExecDestroy(P.step);
+    P.step = nullptr;
+  }
   if (P.H) {
     std::lock_guard<std::recursive_mutex> hl(c.hier_mu);
     std::vector<std::shared_ptr<Hierarchy>> rest;
@@ -538,10 +559,37 @@ int mg_amr2_solve(mg_ctx_t h, mg_fab_t rhs0, mg_fab_t phi0, mg_fab_t rhs1, mg_fa
     if (std::isnan(rhsnorm) || std::isinf(rhsnorm)) {
       status = MG_ENAN;
     } else {
-      for (;;) {
+      // one iteration after the stop test: coarse correction from the composite residual
+      // (r0 is its right-hand side), fine sweeps with coarse/fine ghosts from the corrected
+      // coarse level, average-down; then the composite residual and its norm
+      auto body = [&] {
+        enqueue_correction_cycle(*c, *P.H, s);
+        MG_CK(launch_add_valid(DT_F64, P.add0.rows(), P.add0.nbox, P.add0.nrows, s));
+        MG_CK(launch_prolong_add(DT_F64, P.prolong.rows(), P.prolong.nbox, P.prolong.nrows, s,
+                                 P.prolong.width));
+        for (int k = 0; k < p.nu1 + p.nu2; ++k)
+          for (int color = 0; color < 2; ++color) {
+            fill_fine(*c, P, *f0, *f1, s);
+            MG_CK(launch_rbgs_half(DT_F64, P.fine_smooth.rows(), P.fine_smooth.nbox,
+                                   P.fine_smooth.nrows, color, s, P.fine_direct, nullptr,
+                                   P.fine_smooth.width));
+          }
+        MG_CK(launch_restrict(DT_F64, P.avg_down.rows(), P.avg_down.nbox, P.avg_down.nrows, s));
         enqueue_residual(*c, P, s);
         MG_CK(cudaMemcpyAsync(P.hnorm, dn, 8, cudaMemcpyDeviceToHost, s));
-        MG_CK(cudaStreamSynchronize(s));
+      };
+      // replayed as a graph from the second iteration on (the first, eager, builds every
+      // cached table the iteration uses)
+      const bool graph = p.use_graph && s != nullptr && s != cudaStreamLegacy &&
+                         s != cudaStreamPerThread;
+      if (P.step && P.graph_stream != s) {
+        cudaGraphExecDestroy(P.step);
+        P.step = nullptr;
+      }
+      enqueue_residual(*c, P, s);
+      MG_CK(cudaMemcpyAsync(P.hnorm, dn, 8, cudaMemcpyDeviceToHost, s));
+      MG_CK(cudaStreamSynchronize(s));
+      for (;;) {
         rn = bits2d(P.hnorm[0]);
         if (std::isnan(rn) || std::isinf(rn)) { status = MG_ENAN; break; }
         if (p.fixed_vcycles >= 0) {
@@ -550,20 +598,33 @@ int mg_amr2_solve(mg_ctx_t h, mg_fab_t rhs0, mg_fab_t phi0, mg_fab_t rhs1, mg_fa
           if (rn <= tol * rhsnorm) break;
           if (it == p.max_iter) { status = MG_NOT_CONVERGED; break; }
         }
-        // coarse correction from the composite residual (r0 is its right-hand side)
-        enqueue_correction_cycle(*c, *P.H, s);
-        MG_CK(launch_add_valid(DT_F64, P.add0.rows(), P.add0.nbox, P.add0.nrows, s));
-        MG_CK(launch_prolong_add(DT_F64, P.prolong.rows(), P.prolong.nbox, P.prolong.nrows, s,
-                                 P.prolong.width));
-        // fine sweeps with coarse/fine ghosts from the corrected coarse level
-        for (int k = 0; k < p.nu1 + p.nu2; ++k)
-          for (int color = 0; color < 2; ++color) {
-            fill_fine(*c, P, *f0, *f1, s);
-            MG_CK(launch_rbgs_half(DT_F64, P.fine_smooth.rows(), P.fine_smooth.nbox,
-                                   P.fine_smooth.nrows, color, s, false, nullptr,
-                                   P.fine_smooth.width));
+        if (graph && it >= 1) {
+          if (!P.step) {
+            cudaGraph_t g = nullptr;
+            const long long before = launches_so_far();
+            MG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            try {
+              body();
+            } catch (...) {
+              cudaStreamEndCapture(s, &g);
+              if (g) cudaGraphDestroy(g);
+              count_launches(before - launches_so_far());
+              throw;
+            }
+            MG_CK(cudaStreamEndCapture(s, &g));
+            P.graph_kernels = launches_so_far() - before;  // captured, not executed
+            count_launches(-P.graph_kernels);
+            cudaError_t e = cudaGraphInstantiate(&P.step, g, 0);
+            cudaGraphDestroy(g);
+            MG_CK(e);
+            P.graph_stream = s;
           }
-        MG_CK(launch_restrict(DT_F64, P.avg_down.rows(), P.avg_down.nbox, P.avg_down.nrows, s));
+          MG_CK(cudaGraphLaunch(P.step, s));
+          count_launches(P.graph_kernels);
+        } else {
+          body();
+        }
+        MG_CK(cudaStreamSynchronize(s));
         ++it;
       }
     }

@@ -275,7 +275,7 @@ void launch_fill(Ctx& c, FabObj& f, const mg_bc* bc, cudaStream_t s, int layers)
   MG_CK(launch_copy_tags(f.dtype, P.tags(), P.chunks(), P.nchunks(), f.base, f.lay.ncomp, s));
 }
 
-FaceReads direct_neighbours(const FabObj& f, const int periodic[3]) {
+FaceReads direct_neighbours(const FabObj& f, const int periodic[3], bool outside_ghosts) {
   FaceReads out;
   const BoxArray& ba = f.ba->ba;
   const FabLayout& lay = f.lay;
@@ -308,6 +308,10 @@ FaceReads direct_neighbours(const FabObj& f, const int periodic[3]) {
         const long long ghost = lay.at(ba, (int)b, g[0], g[1], g[2]);
         const int L = ba.dom.len(d);
         if (g[d] < ba.dom.lo[d] || g[d] > ba.dom.hi[d]) {
+          if (!periodic[d] && outside_ghosts) {  // the ghost cell itself
+            dl[b][face] = 0;
+            continue;
+          }
           if (!periodic[d]) {  // -(the box's own boundary layer)
             dl[b][face] = side ? -stride[d] : stride[d];
             fl[b] |= 1 << face;

@@ -140,7 +140,10 @@ struct FaceReads {
     R.nbf = flags[b];
   }
 };
-FaceReads direct_neighbours(const FabObj& f, const int periodic[3]);
+// outside_ghosts: faces on the domain boundary that are not periodic read their own ghost
+// cells (filled by the caller, e.g. coarse/fine ghosts of a refined region) instead of the
+// negated boundary cell.
+FaceReads direct_neighbours(const FabObj& f, const int periodic[3], bool outside_ghosts = false);
 
 struct OpTable {
   DevBufP d;

@@ -162,3 +162,21 @@ def test_refused_layouts(gctx):
     assert e.value.code == mg.MG_EINVAL
     for f in (c0, c1, f0, f1, g0, g1):
         mg.mg_fab_free(gctx, f)
+
+
+@pytest.mark.parametrize("periodic", [(0, 0, 0), (1, 1, 1)])
+def test_graph_replay_equals_eager(gctx, periodic):
+    """From the second iteration on the composite iteration is replayed as a CUDA graph; the
+    answer equals, bit for bit, the one of eager launches."""
+    out = []
+    for use_graph in (1, 0):
+        g, _, F = _setup(gctx, CASES[0], periodic, 93, zero_phi=True)
+        res = mg.mg_amr2_solve(gctx, F["rhs0"], F["phi0"], F["rhs1"], F["phi1"], mg.make_bc(periodic),
+                               1e-10, mg.make_options(use_graph=use_graph))
+        assert res.status == mg.MG_OK and res.vcycles >= 3
+        out.append((res.vcycles, res.rel_resid, gu.fab_dense(gctx, F["phi0"], g.n0[::-1]),
+                    gu.fab_dense(gctx, F["phi1"], g.n1[::-1])))
+        _free(gctx, F)
+    (va, ra, a0, a1), (vb, rb, b0, b1) = out
+    assert va == vb and ra == rb
+    assert np.array_equal(a0, b0) and np.array_equal(a1, b1)
