@@ -97,6 +97,11 @@ typedef struct {
                          filled first ghost layer.  Trilinear runs every level as separate
                          launches (coarse_cells is ignored).  With the 8-cell-average
                          restriction it does not converge faster than injection. */
+  int inner_cycles;   /* MG_PREC_MIXED: FP32 V-cycles on the scaled residual per outer FP64
+                         iteration (1 to 8; 0 = default 2).  Each outer iteration then gains
+                         about the contraction of that many V-cycles, at one FP64 residual
+                         pass, one scaling and one correction; `vcycles` in mg_result counts
+                         outer iterations. */
 } mg_options;
 
 typedef struct {

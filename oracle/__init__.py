@@ -267,9 +267,10 @@ def bottom_matrix(n, periodic, h):
 
 
 def solve(dlo, dhi, periodic, boxes, h, rhs, phi0=None, tol=1e-10, max_iter=50, nu1=2, nu2=2,
-          fixed_vcycles=-1, mixed=False, trilinear=False):
+          fixed_vcycles=-1, mixed=False, trilinear=False, inner_cycles=2):
     """V-cycle solve of A phi = rhs on a dense domain array (nz, ny, nx); trilinear selects
-    the trilinear prolongation.
+    the trilinear prolongation; inner_cycles: FP32 V-cycles per outer iteration of the mixed
+    form (the library's default is 2).
 
     Returns (phi, status, vcycles, hist) where hist[i] is ||rhs - A phi_i||_inf / ||rhs||_inf
     before V-cycle i (and after the last one)."""
@@ -284,7 +285,7 @@ def solve(dlo, dhi, periodic, boxes, h, rhs, phi0=None, tol=1e-10, max_iter=50, 
                        ctypes.c_int(max_iter), ctypes.c_int(nu1), ctypes.c_int(nu2),
                        ctypes.c_int(fixed_vcycles), ctypes.c_int(1 if mixed else 0),
                        ctypes.byref(vc), _dp(hist), ctypes.c_int(len(hist)),
-                       ctypes.c_int(1 if trilinear else 0))
+                       ctypes.c_int(1 if trilinear else 0), ctypes.c_int(inner_cycles))
     if rc == EINVAL:
         raise ValueError("orc_solve: invalid problem")
     return phi, rc, vc.value, hist[:vc.value + 1].copy()

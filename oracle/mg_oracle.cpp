@@ -766,12 +766,14 @@ int orc_bottom_matrix(const int n[3], const int periodic[3], double h, double* M
 // on entry and the result on exit.  fixed_vcycles >= 0 runs exactly that many V-cycles with
 // no stop test.  mixed != 0 selects the FP64-outer / FP32-inner form.  hist receives the
 // relative residual before each V-cycle and after the last (hist_cap entries at most).
-// trilinear != 0 selects the trilinear prolongation.
+// trilinear != 0 selects the trilinear prolongation.  inner (>= 1): FP32 V-cycles per outer
+// iteration of the mixed form, the later ones continuing from the correction so far.
 // Returns ORC_OK, ORC_NOT_CONVERGED, ORC_ENAN or ORC_EINVAL.
 int orc_solve(const int dlo[3], const int dhi[3], const int periodic[3], int nbox, const int* lohi,
               double h, const double* rhs_g, double* phi_g, double tol, int max_iter, int nu1,
               int nu2, int fixed_vcycles, int mixed, int* vcycles, double* hist, int hist_cap,
-              int trilinear) {
+              int trilinear, int inner) {
+  if (inner < 1) return ORC_EINVAL;
   Level L0 = make_level(dlo, dhi, periodic, h, nbox, lohi);
   std::vector<Level> levels;
   if (!build_hierarchy(L0, levels)) return ORC_EINVAL;
@@ -826,7 +828,7 @@ int orc_solve(const int dlo[3], const int dhi[3], const int periodic[3], int nbo
               Df[0].frhs.at((int)b, x, y, z) = (float)(D[0].fr.at((int)b, x, y, z) * down);
       }
       zero_valid(Df[0].fphi);
-      vcycle(Df, Mb, 0, nu1, nu2, trilinear != 0);
+      for (int k = 0; k < inner; ++k) vcycle(Df, Mb, 0, nu1, nu2, trilinear != 0);
       for (size_t b = 0; b < L.boxes.size(); ++b) {
         const Box& B = L.boxes[b];
         for (int z = B.lo[2]; z <= B.hi[2]; ++z)

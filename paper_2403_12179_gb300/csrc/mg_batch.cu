@@ -154,7 +154,7 @@ struct StepLists {
   TagB fill_phi0;
   int dt = DT_F64;
   bool mixed = false;
-  int nu1 = 2, nu2 = 2;
+  int nu1 = 2, nu2 = 2, inner = 1;  // (the members of one step share them)
 };
 
 struct Staging {
@@ -206,6 +206,7 @@ void build_lists(Ctx& c, StepLists& S, const std::vector<Member*>& run,
     S.mixed = H.mixed;
     S.nu1 = H.p.nu1;
     S.nu2 = H.p.nu2;
+    S.inner = H.mixed ? H.p.inner : 1;
     const int nl = (int)H.L.size();
     if (nl == 1) S.bottom0.add(H);
     if (H.lc == 0 && nl > 1) S.coarse0.add(H);
@@ -316,35 +317,38 @@ void enqueue_step(Ctx& c, StepLists& S, const unsigned char* dev, unsigned long 
   if (S.mixed && S.scale0.total) {
     MG_CK(launch_scale_residual_f32_l(mk(S.scale0, dev), S.scale0.total, norms, s));
   }
-  if (!S.bottom0.v.empty())
-    MG_CK(launch_bottom(S.dt, (const BottomJob*)(dev + S.bottom0.off), (int)S.bottom0.v.size(),
-                        S.bottom0.maxN, s));
-  if (!S.coarse0.v.empty())
-    MG_CK(launch_coarse_cycle(S.dt, (const CoarseJob*)(dev + S.coarse0.off),
-                              (int)S.coarse0.v.size(), S.coarse0.smem, s));
-  for (int l = 0; l < nlev; ++l) {
-    LevelLists& LL = S.L[l];
-    if (!LL.rr.total) continue;
-    if (LL.fill_rhs.total) fill_l(c, S.dt, LL.fill_rhs, dev, s);
-    smooth_l(c, S, LL, S.nu1, dev, err, s);
-    fill_l(c, S.dt, LL.fill1_all, dev, s);
-    MG_CK(launch_residual_restrict_l(S.dt, mk(LL.rr, dev), LL.rr.total, s, LL.rr.direct));
-    if (!LL.bottom_next.v.empty())
-      MG_CK(launch_bottom(S.dt, (const BottomJob*)(dev + LL.bottom_next.off),
-                          (int)LL.bottom_next.v.size(), LL.bottom_next.maxN, s));
-    if (!LL.coarse_next.v.empty())
-      MG_CK(launch_coarse_cycle(S.dt, (const CoarseJob*)(dev + LL.coarse_next.off),
-                                (int)LL.coarse_next.v.size(), LL.coarse_next.smem, s));
-  }
-  for (int l = nlev - 1; l >= 0; --l) {
-    LevelLists& LL = S.L[l];
-    if (!LL.prolong.total && !LL.prolong3.total) continue;
-    if (LL.prolong.total) MG_CK(launch_prolong_add_l(S.dt, mk(LL.prolong, dev), LL.prolong.total, s));
-    if (LL.prolong3.total) {
-      fill_l(c, S.dt, LL.fill_c, dev, s);
-      MG_CK(launch_prolong_trilinear_l(S.dt, mk(LL.prolong3, dev), LL.prolong3.total, s));
+  // the V-cycle (mixed form: S.inner FP32 cycles, the later ones from the correction so far)
+  for (int rep = 0; rep < S.inner; ++rep) {
+    if (!S.bottom0.v.empty())
+      MG_CK(launch_bottom(S.dt, (const BottomJob*)(dev + S.bottom0.off), (int)S.bottom0.v.size(),
+                          S.bottom0.maxN, s));
+    if (!S.coarse0.v.empty())
+      MG_CK(launch_coarse_cycle(S.dt, (const CoarseJob*)(dev + S.coarse0.off),
+                                (int)S.coarse0.v.size(), S.coarse0.smem, s));
+    for (int l = 0; l < nlev; ++l) {
+      LevelLists& LL = S.L[l];
+      if (!LL.rr.total) continue;
+      if (LL.fill_rhs.total) fill_l(c, S.dt, LL.fill_rhs, dev, s);
+      smooth_l(c, S, LL, S.nu1, dev, err, s);
+      fill_l(c, S.dt, LL.fill1_all, dev, s);
+      MG_CK(launch_residual_restrict_l(S.dt, mk(LL.rr, dev), LL.rr.total, s, LL.rr.direct));
+      if (!LL.bottom_next.v.empty())
+        MG_CK(launch_bottom(S.dt, (const BottomJob*)(dev + LL.bottom_next.off),
+                            (int)LL.bottom_next.v.size(), LL.bottom_next.maxN, s));
+      if (!LL.coarse_next.v.empty())
+        MG_CK(launch_coarse_cycle(S.dt, (const CoarseJob*)(dev + LL.coarse_next.off),
+                                  (int)LL.coarse_next.v.size(), LL.coarse_next.smem, s));
     }
-    smooth_l(c, S, LL, S.nu2, dev, err, s);
+    for (int l = nlev - 1; l >= 0; --l) {
+      LevelLists& LL = S.L[l];
+      if (!LL.prolong.total && !LL.prolong3.total) continue;
+      if (LL.prolong.total) MG_CK(launch_prolong_add_l(S.dt, mk(LL.prolong, dev), LL.prolong.total, s));
+      if (LL.prolong3.total) {
+        fill_l(c, S.dt, LL.fill_c, dev, s);
+        MG_CK(launch_prolong_trilinear_l(S.dt, mk(LL.prolong3, dev), LL.prolong3.total, s));
+      }
+      smooth_l(c, S, LL, S.nu2, dev, err, s);
+    }
   }
   if (S.mixed && S.correct0.total)
     MG_CK(launch_correct_add_l(mk(S.correct0, dev), S.correct0.total, norms, s));
@@ -518,9 +522,10 @@ struct Ctx::Server {
   size_t max_queue = 1 << 20;
   int max_active = 4096;
   mg_server_stats stats{};
-  // norm slots of the FP64 [0] and mixed-precision [1] members (separate: each group's
-  // check clears its whole array, and a mixed member's next step reads its last norm)
-  NormBuf norms[2];
+  // norm slots per step group -- members of one precision, smoothing counts and inner
+  // cycles, which share their steps (separate arrays: each group's check clears its whole
+  // array, and a mixed member's next step reads its last norm)
+  std::map<std::array<int, 4>, NormBuf> norms;
 };
 
 
@@ -731,12 +736,21 @@ void server_loop(Ctx* c) {
       S.stats.max_active = std::max<int64_t>(S.stats.max_active, (int64_t)active.size());
     }
     try {
-      // one step per precision group: running members cycle, every member's norm is checked
-      for (int dt : {DT_F64, DT_F32}) {
-        NormBuf& nb = S.norms[dt == DT_F64 ? 0 : 1];
+      // one step per group (precision, smoothing counts, inner cycles): running members
+      // cycle, every member's norm is checked
+      auto key_of = [](const Member& m) {
+        const SolveParams& p = m.H->p;
+        return std::array<int, 4>{m.H->dt, p.nu1, p.nu2, m.H->mixed ? p.inner : 1};
+      };
+      std::vector<std::array<int, 4>> keys;
+      for (auto& m : active)
+        if (!m->done && std::find(keys.begin(), keys.end(), key_of(*m)) == keys.end())
+          keys.push_back(key_of(*m));
+      for (const auto& key : keys) {
+        NormBuf& nb = S.norms[key];
         std::vector<Member*> run, check;
         for (auto& m : active) {
-          if (m->done || m->H->dt != dt) continue;
+          if (m->done || key_of(*m) != key) continue;
           check.push_back(m.get());
           if (m->started) run.push_back(m.get());
         }
@@ -840,7 +854,7 @@ void server_loop(Ctx* c) {
   while (evict_idle(*c, S, s)) {
   }
   if (st.dev) st.dev->reset(s);
-  for (NormBuf& nb : S.norms) nb.release(s);
+  for (auto& kv : S.norms) kv.second.release(s);
   cudaStreamSynchronize(s);
   if (cs != s) cudaStreamDestroy(cs);
 }
@@ -896,7 +910,7 @@ int server_submit_host(Ctx& c, std::shared_ptr<BoxArrayObj> ba, const double* rh
     for (const Box& b : ba->ba.boxes) put(&b, sizeof(Box));
     put(bc, sizeof(mg_bc));
     const int ip[8] = {p.nu1, p.nu2, p.precision, p.smoother, p.coarse_cells, p.direct_reads,
-                       p.prolong, 0};
+                       p.prolong, p.inner};
     put(ip, sizeof ip);
     put(&p.h, sizeof p.h);
   }

@@ -622,6 +622,7 @@ SolveParams params_from(const mg_options* o, const BoxArray& ba) {
     p.coarse_cells = o->coarse_cells;
     p.direct_reads = o->direct_reads;
     p.prolong = o->prolong;
+    p.inner = o->inner_cycles == 0 ? kDefaultInnerCycles : o->inner_cycles;
   }
   if (p.h <= 0.0) p.h = 1.0 / ba.dom.len(0);
   if (p.nu1 < 0 || p.nu2 < 0 || p.max_iter < 0 || p.nu1 + p.nu2 == 0)
@@ -632,6 +633,7 @@ SolveParams params_from(const mg_options* o, const BoxArray& ba) {
     fail(MG_EINVAL, "unknown smoother");
   if (p.prolong != MG_PROLONG_CONSTANT && p.prolong != MG_PROLONG_TRILINEAR)
     fail(MG_EINVAL, "unknown prolongation");
+  if (p.inner < 1 || p.inner > kMaxInnerCycles) fail(MG_EINVAL, "inner_cycles out of range");
   return p;
 }
 

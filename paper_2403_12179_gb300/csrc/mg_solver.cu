@@ -243,7 +243,7 @@ Hierarchy& get_hierarchy(Ctx& c, FabObj& rhs, FabObj& phi, const mg_bc* bc, cons
         h->p.nu1 == p.nu1 && h->p.nu2 == p.nu2 && h->p.precision == p.precision &&
         h->p.smoother == p.smoother && h->p.h == p.h &&
         h->p.coarse_cells == p.coarse_cells && h->p.direct_reads == p.direct_reads &&
-        h->p.prolong == p.prolong)
+        h->p.prolong == p.prolong && h->p.inner == p.inner)
       return *h;
   }
   if (rhs.dtype != DT_F64 || phi.dtype != DT_F64) fail(MG_EINVAL, "mg_solve needs FP64 fabs");
@@ -473,6 +473,8 @@ void enqueue_step(Ctx& c, Hierarchy& H, cudaStream_t s, int variant) {
   }
   if (split_norm) MG_CK(cudaMemsetAsync(dn, 0, 8, s));
   enqueue_vcycle(c, H, s, split_norm ? dn : nullptr);
+  if (H.mixed)  // the further FP32 cycles of the outer iteration, from the correction so far
+    for (int k = 1; k < H.p.inner; ++k) enqueue_vcycle(c, H, s, nullptr);
   if (H.mixed)
     MG_CK(launch_correct_add(H.correct0.rows(), H.correct0.nbox, H.correct0.nrows, dn, s,
                              H.correct0.width));

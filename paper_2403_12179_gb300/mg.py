@@ -39,7 +39,8 @@ class mg_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("fixed_vcycles", ctypes.c_int),
                 ("h", ctypes.c_double), ("coarse_cells", ctypes.c_int),
-                ("direct_reads", ctypes.c_int), ("prolong", ctypes.c_int)]
+                ("direct_reads", ctypes.c_int), ("prolong", ctypes.c_int),
+                ("inner_cycles", ctypes.c_int)]
 
 
 class mg_result(ctypes.Structure):
@@ -107,9 +108,9 @@ def make_bc(periodic=(1, 1, 1)):
 
 def make_options(nu1=2, nu2=2, max_iter=50, precision=MG_PREC_F64, smoother=MG_SMOOTH_AUTO,
                  use_graph=1, fixed_vcycles=-1, h=0.0, coarse_cells=0, direct_reads=1,
-                 prolong=MG_PROLONG_CONSTANT):
+                 prolong=MG_PROLONG_CONSTANT, inner_cycles=0):
     return mg_options(nu1, nu2, max_iter, precision, smoother, use_graph, fixed_vcycles, h,
-                      coarse_cells, direct_reads, prolong)
+                      coarse_cells, direct_reads, prolong, inner_cycles)
 
 
 # ---- context -------------------------------------------------------------------------

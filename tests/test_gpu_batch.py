@@ -40,10 +40,11 @@ def _make(ctx, n, box, periodic, seed, ng=(2, 1)):
 
 
 def _alone(ctx, n, box, periodic, seed, precision, smoother=mg.MG_SMOOTH_AUTO,
-           prolong=mg.MG_PROLONG_CONSTANT):
+           prolong=mg.MG_PROLONG_CONSTANT, **opts):
     rhs, fr, fp = _make(ctx, n, box, periodic, seed)
     res = mg.mg_solve(ctx, fr, fp, mg.make_bc(periodic), 1e-10,
-                      mg.make_options(precision=precision, smoother=smoother, prolong=prolong))
+                      mg.make_options(precision=precision, smoother=smoother, prolong=prolong,
+                                      **opts))
     phi = gu.fab_dense(ctx, fp, rhs.shape)
     mg.mg_fab_free(ctx, fr)
     mg.mg_fab_free(ctx, fp)
@@ -122,7 +123,8 @@ def test_serving_results_equal_alone(precision):
 def test_serving_many_members_both_precisions_equal_alone():
     """More members than the initial norm slots hold (the arrays grow while members run),
     FP64 and mixed-precision members (half-sweep and fused smoothers, injection and trilinear
-    prolongation) at once, later requests joining running ones: every result and V-cycle
+    prolongation, one to three inner cycles, V(2,2) and V(1,1) -- members that step in
+    separate groups) at once, later requests joining running ones: every result and V-cycle
     count equals the solve alone."""
     ctx = mg.mg_init(0)
     actx = mg.mg_init(0)
@@ -132,22 +134,27 @@ def test_serving_many_members_both_precisions_equal_alone():
         precs = [mg.MG_PREC_F64 if i % 3 == 0 else mg.MG_PREC_MIXED for i in range(count)]
         smooth = [mg.MG_SMOOTH_FUSED if i % 3 == 2 else mg.MG_SMOOTH_AUTO for i in range(count)]
         prol = [mg.MG_PROLONG_TRILINEAR if i % 4 == 3 else mg.MG_PROLONG_CONSTANT for i in range(count)]
+        extra = [dict(inner_cycles=(i // 2) % 4, nu1=1 + (i % 5 == 4), nu2=1 + (i % 5 == 4))
+                 if i % 2 else {} for i in range(count)]
         made, tickets = [], []
         for i, ((n, b, p), pr) in enumerate(zip(specs, precs)):
             m = _make(ctx, n, b, p, 400 + i)
             made.append(m)
             tickets.append(mg.mg_submit(ctx, m[1], m[2], mg.make_bc(p), 1e-10,
                                         mg.make_options(precision=pr, smoother=smooth[i],
-                                                        prolong=prol[i])))
+                                                        prolong=prol[i], **extra[i])))
             if i % 12 == 11:
                 time.sleep(0.02)
         res = [mg.mg_poll(ctx, t, -1)[1] for t in tickets]
         stats = mg.mg_server_stats_get(ctx)
         assert stats["completed"] == count
         for i, ((n, b, p), pr, (rhs, fr, fp), r) in enumerate(zip(specs, precs, made, res)):
-            assert r.status == mg.MG_OK and r.rel_resid <= 1e-10
             phi = gu.fab_dense(ctx, fp, rhs.shape)
-            phi_a, res_a = _alone(actx, n, b, p, 400 + i, pr, smooth[i], prol[i])
+            phi_a, res_a = _alone(actx, n, b, p, 400 + i, pr, smooth[i], prol[i], **extra[i])
+            # (V(1,1) with injection does not reach 1e-10 in 50 cycles on some of these
+            # problems: the served solve must then stop the same way)
+            assert r.status == res_a.status, (i, n, b, p, pr, extra[i])
+            assert r.status != mg.MG_OK or r.rel_resid <= 1e-10
             assert res_a.vcycles == r.vcycles, (i, n, b, p, pr)
             assert np.array_equal(phi, phi_a)
     finally:

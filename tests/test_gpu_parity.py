@@ -692,12 +692,16 @@ def test_fused_sweep_rhs_staging_forced(orc, tmp_path, monkeypatch, rhs_smem, ty
 # below 256^3), the fused sweep on every level but the bottom, and the fused sweep with the
 # one-launch coarse cycle switched off (fused sweeps down to 4^3).
 
-MIXED_ITER_CASES = [(mg.MG_SMOOTH_AUTO, 0), (mg.MG_SMOOTH_FUSED, 0), (mg.MG_SMOOTH_FUSED, -1)]
+MIXED_ITER_CASES = [(mg.MG_SMOOTH_AUTO, 0, 0), (mg.MG_SMOOTH_FUSED, 0, 0),
+                    (mg.MG_SMOOTH_FUSED, -1, 0), (mg.MG_SMOOTH_AUTO, 0, 1),
+                    (mg.MG_SMOOTH_FUSED, 0, 3)]
 
 
-@pytest.mark.parametrize("smoother,coarse", MIXED_ITER_CASES)
+@pytest.mark.parametrize("smoother,coarse,inner", MIXED_ITER_CASES)
 @pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (0, 1, 1)])
-def test_mixed_iterates_match_oracle_bitwise(gctx, orc, smoother, coarse, periodic):
+def test_mixed_iterates_match_oracle_bitwise(gctx, orc, smoother, coarse, inner, periodic):
+    """Mixed-form iterates (FP32 inner cycles, inner = 0: the default two) equal the
+    oracle's bit for bit after 1, 2 and 3 outer iterations."""
     n, mb = 32, (16, 16, 16)
     dom = (n - 1,) * 3
     rhs = inputs.rng(46).standard_normal((n, n, n))
@@ -709,12 +713,12 @@ def test_mixed_iterates_match_oracle_bitwise(gctx, orc, smoother, coarse, period
     for k in (1, 2, 3):
         fp = mg.mg_fab_alloc(gctx, ba, 1, 2)
         opt = mg.make_options(precision=mg.MG_PREC_MIXED, fixed_vcycles=k, smoother=smoother,
-                              coarse_cells=coarse)
+                              coarse_cells=coarse, inner_cycles=inner)
         res = mg.mg_solve(gctx, fr, fp, mg.make_bc(periodic), 1e-10, opt)
         phi = gu.fab_dense(gctx, fp, rhs.shape)
         mg.mg_fab_free(gctx, fp)
         o_phi, st, vc, _ = orc.solve(Z3, dom, periodic, boxes, 1.0 / n, rhs, fixed_vcycles=k,
-                                     mixed=True)
+                                     mixed=True, inner_cycles=inner or 2)
         assert res.status == mg.MG_OK and res.vcycles == vc == k
         assert np.array_equal(phi, o_phi), (k, np.abs(phi - o_phi).max())
     mg.mg_fab_free(gctx, fr)

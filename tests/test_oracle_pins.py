@@ -447,12 +447,14 @@ def test_vcycle_schedule_matches_dense_composition(orc, n, mb, periodic, nu):
 
 @pytest.mark.parametrize("n,mb", VC_CASES)
 @pytest.mark.parametrize("periodic", VC_FACES)
-def test_mixed_outer_iteration_matches_dense_composition(orc, n, mb, periodic):
-    """The mixed form's outer iteration phi <- phi + V(rhs - A phi) (the inner cycle on the
-    residual scaled by an exact power of two, then scaled back) equals the FP64 dense cycle
-    applied to the residual, up to the inner cycle's binary32 rounding: each inner value
-    carries a few units of 2^-24 relative to the correction, so the bound is 2^-20 of the
-    largest correction."""
+@pytest.mark.parametrize("inner", [1, 2, 3])
+def test_mixed_outer_iteration_matches_dense_composition(orc, n, mb, periodic, inner):
+    """The mixed form's outer iteration phi <- phi + e, e = m inner cycles on A e = r from
+    e = 0 (r = rhs - A phi scaled by an exact power of two, e scaled back), equals m FP64
+    dense cycles from phi -- a V-cycle is the affine map phi + B (rhs - A phi), so its m-fold
+    application from 0 on the residual equation adds exactly what m cycles from phi add --
+    up to the inner cycles' binary32 rounding: each inner value carries a few units of 2^-24
+    relative to the correction, so the bound is 2^-20 of the largest correction."""
     h = 1.0 / n[0]
     dlo, dhi = _dom(n)
     boxes = orc.chop(dlo, dhi, mb)
@@ -460,8 +462,8 @@ def test_mixed_outer_iteration_matches_dense_composition(orc, n, mb, periodic):
     ref = dense_ref.DenseVCycle(n, periodic, h)
     for k in (1, 2):
         phi, st, vc, _ = orc.solve(dlo, dhi, periodic, boxes, h, rhs, phi0=phi0, fixed_vcycles=k,
-                                   mixed=True)
-        d = ref.run(phi0, rhs, k)
+                                   mixed=True, inner_cycles=inner)
+        d = ref.run(phi0, rhs, k * inner)
         assert st == 0 and vc == k
         assert np.abs(phi - d).max() <= 2.0 ** -20 * np.abs(d - phi0).max()
 
