@@ -277,7 +277,7 @@ __device__ __forceinline__ T tag_value(const T* p, int sign) {
 template <class T, int NC>
 __global__ void __launch_bounds__(256) k_copy_tags(TagList L, long long nchunks, int ncomp) {
   pdl_begin();
-  constexpr int U = (NC == 1 ? kTagChunk1 : kTagChunkN) / 32;
+  constexpr int U = (NC == 1 ? (sizeof(T) == 4 ? kTagChunk1F : kTagChunk1) : kTagChunkN) / 32;
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (w >= nchunks) return;
   const int lane = threadIdx.x & 31;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256) k_copy_tags(TagList L, long long nchunks,
   if (L.n > 1) S = L.segs[find_tagseg(L.segs, L.n, w)];
   const int2 ch = S.chunks[w - S.chunk_begin];
   const DTag t = S.tags[ch.x];
-  const int r1 = min(ch.y + tag_chunk_rows(t.ex, ncomp), t.ey * t.ez);
+  const int r1 = min(ch.y + tag_chunk_rows(t.ex, ncomp, (int)sizeof(T)), t.ey * t.ez);
   const int ncell = (r1 - ch.y) * t.ex;
   T* __restrict__ base = (T*)S.base;
   const int nc = NC ? NC : ncomp;
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256, 3) k_copy_tags_multi(TagList L, long long
   if (L.n > 1) S = L.segs[find_tagseg(L.segs, L.n, w)];
   const int2 ch = S.chunks[w - S.chunk_begin];
   const DTag t = S.tags[ch.x];
-  const int r1 = min(ch.y + tag_chunk_rows(t.ex, ncomp), t.ey * t.ez);
+  const int r1 = min(ch.y + tag_chunk_rows(t.ex, ncomp, (int)sizeof(T)), t.ey * t.ez);
   const int ncell = (r1 - ch.y) * t.ex;
   const T* __restrict__ src = (const T*)S.base + t.src;
   T* __restrict__ dst = (T*)S.base + t.dst;

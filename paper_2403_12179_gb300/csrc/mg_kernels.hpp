@@ -95,12 +95,14 @@ struct CoarseJob {
 };
 
 // The copy-tag kernel gives each warp a chunk of whole x-rows of one tag: about kTagChunk1
-// destination cells for one-component fabs, kTagChunkN for more (measured best on GB300),
+// destination cells for one-component FP64 fabs, kTagChunk1F for one-component FP32 fabs
+// (the mixed form's fused levels: 512^3 mixed solve 59.8 -> 59.2 ms against 64), kTagChunkN
+// for more components (measured best on GB300),
 // at least one row.  Chunks are int2 {tag, first row}; host and device derive a chunk's row
-// count from the tag's x-extent and the fab's components with tag_chunk_rows.
-constexpr int kTagChunk1 = 64, kTagChunkN = 128;
-__host__ __device__ inline int tag_chunk_rows(int ex, int ncomp) {
-  const int cells = ncomp == 1 ? kTagChunk1 : kTagChunkN;
+// count from the tag's x-extent, the fab's components and element size with tag_chunk_rows.
+constexpr int kTagChunk1 = 64, kTagChunk1F = 256, kTagChunkN = 128;
+__host__ __device__ inline int tag_chunk_rows(int ex, int ncomp, int esize = 8) {
+  const int cells = ncomp == 1 ? (esize == 4 ? kTagChunk1F : kTagChunk1) : kTagChunkN;
   return ex >= cells ? 1 : cells / ex;
 }
 

@@ -246,7 +246,7 @@ FillPlan& fill_plan(Ctx& c, FabObj& f, const mg_bc* bc, int layers) {
     std::vector<int> first;
     for (size_t t = 0; t < dt.size(); ++t) {
       first.push_back((int)chunks.size());
-      const int rows = dt[t].ey * dt[t].ez, per = tag_chunk_rows(dt[t].ex, f.lay.ncomp);
+      const int rows = dt[t].ey * dt[t].ez, per = tag_chunk_rows(dt[t].ex, f.lay.ncomp, f.esize());
       for (int r0 = 0; r0 < rows; r0 += per) chunks.push_back(make_int2((int)t, r0));
     }
     first.push_back((int)chunks.size());
