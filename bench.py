@@ -50,13 +50,13 @@ WORKLOADS = {
                             "U(-1e-3,1e-3) seed 1, mean removed, V(2,2), tol 1e-10"),
     "mixed256": dict(n=256, box=64, periodic=(0, 0, 0), precision="mixed",
                      desc="256^3 homogeneous Dirichlet, 64 boxes of 64^3, rhs = N(0,1) seed 2 "
-                          "smoothed by one damped-Jacobi pass, FP32 inner V(2,2) / FP64 outer "
-                          "residual, correction and bottom, tol 1e-10 (a smaller mixed case, for "
-                          "profiling)"),
+                          "smoothed by one damped-Jacobi pass, FP32 inner V(2,2) (2 per outer "
+                          "iteration) / FP64 outer residual, correction and bottom, tol 1e-10 (a "
+                          "smaller mixed case, for profiling)"),
     "mixed512": dict(n=512, box=128, periodic=(0, 0, 0), precision="mixed",
                      desc="512^3 homogeneous Dirichlet, 64 boxes of 128^3, 16 Gaussian blobs + "
-                          "N(0,1e-3) seed 5, FP32 inner V(2,2) / FP64 outer residual, correction "
-                          "and bottom, tol 1e-10"),
+                          "N(0,1e-3) seed 5, FP32 inner V(2,2) (2 per outer iteration) / FP64 "
+                          "outer residual, correction and bottom, tol 1e-10"),
 }
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 
