@@ -399,8 +399,9 @@ __device__ __forceinline__ void flush_block_max(unsigned long long mx, int cur,
 // (as MODE 1 takes it) stored to v[2], for the residual + restriction that follows
 // (k_residual_restrict with STORED).
 // MODE 4 (plain, as MODE 0): four cells of a lane per step with all loads first, for FP32
-// launches over rows of at least 64 cells (measured on GB300: 256^3 FP32 half-sweep 45.5 ->
-// 42.5 us; on 32-wide rows the two-cell form is faster).
+// launches over rows of 64 to 127 cells (measured on GB300: 64-wide boxes, 256^3 FP32
+// half-sweep 45.5 -> 42.5 us; the two-cell form is faster on 32-wide rows, and on 128-wide
+// ones: 512^3 454 against 492 us).
 // v[2] of MODE 2 / 3 is a one-colour view: cell x of row (y, z) at element x / 2 of the row
 // (two cells of one colour are never neighbours in x), so that a warp's stores fill whole
 // sectors instead of every other element of sectors it has not read.
@@ -1077,8 +1078,9 @@ cudaError_t launch_rbgs_half_l(int dt, const SegList& L, long long nrows, int co
   if (nrows <= 0) return cudaSuccess;
   if (norms && (L.n != 1 || !direct)) return cudaErrorInvalidValue;
   if (pre && !norms) return cudaErrorInvalidValue;
-  // a line of w cells holds w / 2 of one colour; two per lane (four on wide FP32 rows)
-  const bool quad = dt == DT_F32 && !norms && L.width >= 64;
+  // a line of w cells holds w / 2 of one colour; two per lane (four on FP32 rows of 64 to
+  // 127 cells)
+  const bool quad = dt == DT_F32 && !norms && L.width >= 64 && L.width < 128;
   const int G = quad ? group_lanes(L.width, 8, 4, 16) : group_lanes(L.width, 4, norms ? 8 : 4, 16);
   const Grid g = row_grid(nrows, row_blocks_per_sm(L.width), kWarps * (32 / G));
   if (norms) {
