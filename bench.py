@@ -280,7 +280,7 @@ def run_ours(args, wl_name):
     # pinned host memory and its phi out to pinned host memory.  Two fab sets, the copies on a
     # stream of their own: step k+1's copy in and step k-1's copy out run while step k solves
     # (the first copy in and the last copy out are exposed).
-    e2e_steps = max(2, min(args.steps, 12))
+    e2e_steps = max(2, min(args.steps, 6))
     cstream = torch.cuda.Stream()
     sets = [(fr, fp), (mg.mg_fab_alloc(ctx, ba, 1, 1), mg.mg_fab_alloc(ctx, ba, 1, 2))]
     outs = [out_host, torch.empty_like(rhs_host).pin_memory()]
